@@ -1,0 +1,165 @@
+/*
+ * gbc.h -- C ABI of the GB300 (sm_103a) exact (p,q)-biclique counter.
+ *
+ * Problem (Sec. II, Def. 1 and the problem statement): given a bipartite graph
+ * G = (U, V, E) and integers p, q, return the number of bicliques B(L, R) with
+ * L a subset of U, R a subset of V, |L| = p, |R| = q and every (u, v) in L x R an
+ * edge.  The count is exact, as an unsigned 128-bit integer.
+ *
+ * Method (Sec. III-A Basic model, Sec. IV Alg. 1, Def. 2): one side is the
+ * anchor; every anchor vertex u roots a search tree that grows the sets L whose
+ * lowest-ranked member is u from u's higher-ranked q-strength 2-hop neighbours
+ * (Sec. II, N_2^q), keeps the common neighbourhood C_R as a bitmap over the
+ * positions of N(u) and the candidates C_L as a bitmap over the root's
+ * candidate list, intersects by word-wise AND plus popcount, and at |L| = p adds
+ * C(|C_R|, q).  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every call:
+ *   - every call returns a gbc_status; outputs are written only on GBC_OK;
+ *     gbc_last_error() then describes the last failure of the calling thread;
+ *   - no call throws, aborts or exits the process;
+ *   - pointers documented as "host" are ordinary CPU memory, borrowed for the
+ *     duration of the call only; "device" pointers are CUDA global memory of
+ *     the context's device, also borrowed for the call only;
+ *   - CSR arrays are int32: off[n+1] with off[0] = 0 and off[n] = |E|,
+ *     adj[|E|] with each row strictly increasing (sorted, no duplicates) and in
+ *     range; the V-side CSR must be the exact transpose of the U-side CSR;
+ *   - 1 <= p, q <= GBC_MAX_PQ, else GBC_ERR_ARG; p > |U| or q > |V| is not an
+ *     error and gives 0;
+ *   - calls on one context are serialised internally (thread-safe).
+ */
+#ifndef GBC_H
+#define GBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBC_MAX_PQ 16
+
+/* Unsigned 128-bit count: value = hi * 2^64 + lo. */
+typedef struct { uint64_t lo, hi; } gbc_u128;
+
+typedef struct gbc_ctx_s   *gbc_ctx_t;
+typedef struct gbc_graph_s *gbc_graph_t;
+
+typedef enum {
+    GBC_OK = 0,
+    GBC_ERR_ARG = 1,            /* bad argument (null pointer, p or q out of range, ...) */
+    GBC_ERR_INVALID_GRAPH = 2,  /* CSR not sorted / not in range / not transposes      */
+    GBC_ERR_OOM = 3,            /* device memory or the context's budget exhausted     */
+    GBC_ERR_OVERFLOW = 4,       /* the count, or one binomial term, exceeds 2^128 - 1   */
+    GBC_ERR_TIMEOUT = 5,        /* a bounded device wait or gbc_poll timed out           */
+    GBC_ERR_CUDA = 6,           /* a CUDA runtime call failed                           */
+    GBC_PENDING = 7,            /* gbc_poll: the request has not finished yet           */
+    GBC_ERR_REJECTED = 8        /* admission refused (queue full / over budget)         */
+} gbc_status;
+
+/* Anchor side: which side's vertices root the search trees (the count does not
+ * depend on it; Sec. III-A footnote, layer selection deferred to the cost model). */
+typedef enum { GBC_ANCHOR_AUTO = 0, GBC_ANCHOR_U = 1, GBC_ANCHOR_V = 2 } gbc_anchor;
+
+/*
+ * gbc_ctx_create -- bind a context to CUDA device `device` with a device-memory
+ * budget for search scratch (bytes; 0 = 80% of the device's free memory).
+ * The context owns one CUDA stream.  Errors: GBC_ERR_ARG (bad device / null
+ * out), GBC_ERR_CUDA.
+ */
+gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out);
+
+/* Use the caller's CUDA stream (a cudaStream_t passed as void*; NULL = the
+ * context's own stream) for every later call on this context. */
+gbc_status gbc_ctx_set_stream(gbc_ctx_t ctx, void *stream);
+
+/* Release the context (its graphs must be freed first). */
+void gbc_ctx_destroy(gbc_ctx_t ctx);
+
+/*
+ * gbc_load_graph -- copy a bipartite graph given as CSR on both sides (host
+ * arrays) to the device, validate it there and build the per-side index the
+ * search uses (Sec. V: neighbour lists re-sorted by the anchor-side priority
+ * of Def. 2, with the mirror position of every edge).
+ *   nU, nV            vertex counts (>= 0)
+ *   offU [nU+1], adjU [|E|]   U -> V adjacency (host)
+ *   offV [nV+1], adjV [|E|]   V -> U adjacency (host), the transpose of U's
+ * The graph handle owns its device memory until gbc_free_graph.
+ * Errors: GBC_ERR_ARG, GBC_ERR_INVALID_GRAPH, GBC_ERR_OOM, GBC_ERR_CUDA.
+ */
+gbc_status gbc_load_graph(gbc_ctx_t ctx, int32_t nU, int32_t nV,
+                          const int32_t *offU, const int32_t *adjU,
+                          const int32_t *offV, const int32_t *adjV,
+                          gbc_graph_t *out);
+
+/* As gbc_load_graph, but the four arrays are device pointers (borrowed; the
+ * graph keeps its own copy). */
+gbc_status gbc_load_graph_device(gbc_ctx_t ctx, int32_t nU, int32_t nV,
+                                 const int32_t *offU_d, const int32_t *adjU_d,
+                                 const int32_t *offV_d, const int32_t *adjV_d,
+                                 gbc_graph_t *out);
+
+/* Release a graph's device memory. */
+void gbc_free_graph(gbc_graph_t g);
+
+/* Basic facts of a loaded graph (host outputs; any may be NULL). */
+gbc_status gbc_graph_info(gbc_graph_t g, int32_t *nU, int32_t *nV, int64_t *nE,
+                          int32_t *max_deg_u, int32_t *max_deg_v);
+
+/*
+ * gbc_count -- exact number of (p,q)-bicliques of g (blocking).
+ * out: host.  Errors: GBC_ERR_ARG, GBC_ERR_OVERFLOW (count >= 2^128),
+ * GBC_ERR_OOM (scratch over the context budget), GBC_ERR_CUDA.
+ */
+gbc_status gbc_count(gbc_graph_t g, int p, int q, gbc_u128 *out);
+
+/* Options of gbc_count_ex; zero-initialise for the defaults. */
+typedef struct {
+    int32_t anchor;      /* gbc_anchor; GBC_ANCHOR_AUTO = cost model picks */
+    int32_t collect_stats; /* 1: fill gbc_count_info's search-tree counters (slower) */
+    int32_t enum_warps;  /* warps of the persistent enumeration launch; 0 = auto */
+    int32_t time_limit_ms; /* > 0: device-side deadline; past it the kernels stop and the
+                              call returns GBC_ERR_TIMEOUT (the count is then not valid) */
+    int32_t reserved[4];
+} gbc_count_options;
+
+/* Facts about one count (host output of gbc_count_ex). */
+typedef struct {
+    int32_t anchor_used;        /* GBC_ANCHOR_U or GBC_ANCHOR_V */
+    int32_t set_size;           /* |L| enumerated on the anchor side */
+    int64_t roots;              /* anchor vertices with >= set_size-1 candidates */
+    int64_t candidates;         /* sum over roots of |C_L| at the root */
+    int64_t units;              /* level-2 work units handed to the enumeration */
+    int64_t evals[GBC_MAX_PQ + 1];  /* children evaluated, by |L| of the child (stats) */
+    int64_t passed[GBC_MAX_PQ + 1]; /* children with |C_R| >= q, by |L| (stats)       */
+    int64_t words_r;            /* C_R words of the tree (stats) */
+    int64_t words_l;            /* C_L words of the tree (stats) */
+    int64_t scratch_bytes;      /* device scratch used by this count */
+    float ms_candidates;        /* device time: 2-hop candidates + bitmap rows */
+    float ms_pairs;             /* device time: pairwise rows (C_L bitmaps) */
+    float ms_enumerate;         /* device time: enumeration kernel */
+    float ms_total;             /* device time of the whole count */
+} gbc_count_info;
+
+/* gbc_count with options and facts (either pointer may be NULL). */
+gbc_status gbc_count_ex(gbc_graph_t g, int p, int q, const gbc_count_options *opt,
+                        gbc_u128 *out, gbc_count_info *info);
+
+/*
+ * gbc_count_per_root -- the count split by search-tree root: per_root[a] is the
+ * number of (p,q)-bicliques whose lowest-ranked anchor-side vertex (rank key
+ * (degree, id), Def. 2 reading) is a.  anchor must be GBC_ANCHOR_U or _V;
+ * per_root: host array of |anchor side| entries.  The sum equals gbc_count.
+ */
+gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor,
+                              gbc_u128 *per_root, gbc_u128 *total);
+
+/* Human-readable text of a status, and the calling thread's last error. */
+const char *gbc_status_string(gbc_status s);
+const char *gbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBC_H */

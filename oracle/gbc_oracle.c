@@ -239,10 +239,11 @@ static int count_root(const view_t *g, int32_t u, u128 *out, int *ovf, orc_stats
         if (!t.rsets[i]) { rc = ORC_NOMEM; goto done; }
         t.rlen[i] = intersect(g->adjA + g->offA[w], dw, nu, d, t.rsets[i]);
     }
-    for (int i = 0; i < c; ++i)
-        for (int j = i + 1; j < c; ++j)
-            t.compat[(size_t)i * c + j] = t.compat[(size_t)j * c + i] =
-                intersect(t.rsets[i], t.rlen[i], t.rsets[j], t.rlen[j], NULL) >= g->q;
+    if (g->p >= 3)  /* the 2-hop relation among candidates is only read below level 2 */
+        for (int i = 0; i < c; ++i)
+            for (int j = i + 1; j < c; ++j)
+                t.compat[(size_t)i * c + j] = t.compat[(size_t)j * c + i] =
+                    intersect(t.rsets[i], t.rlen[i], t.rsets[j], t.rlen[j], NULL) >= g->q;
     for (int i = 0; i < c; ++i) cl0[i] = i;
     expand(&t, 1, nu, d, cl0, c);
     *out = t.acc;

@@ -1,0 +1,251 @@
+"""GB300 (sm_103a) exact (p,q)-biclique counting: Python binding of libgbc.so.
+
+The binding only marshals arguments: every step of a count runs in the CUDA
+kernels behind the C ABI of include/gbc.h.  There is no CPU fallback; if the
+library has not been built, or no GPU is present, the calls raise.
+
+    import paper_2403_07858_gb300 as gbc
+    ctx = gbc.Context()                       # device 0
+    g = ctx.load_graph(n_u, n_v, off_u, adj_u, off_v, adj_v)   # host arrays
+    n = g.count(4, 4)                         # Python int, exact
+    n, info = g.count_ex(4, 4, anchor="V", stats=True)
+
+Arrays may be numpy arrays (host) or CUDA torch tensors (``load_graph`` copies
+either way; torch is only used for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbc.so")
+MAX_PQ = 16
+
+GBC_OK, GBC_ERR_ARG, GBC_ERR_INVALID_GRAPH, GBC_ERR_OOM, GBC_ERR_OVERFLOW = 0, 1, 2, 3, 4
+GBC_ERR_TIMEOUT, GBC_ERR_CUDA, GBC_PENDING, GBC_ERR_REJECTED = 5, 6, 7, 8
+ANCHORS = {"auto": 0, "U": 1, "V": 2}
+_ANCHOR_NAMES = {1: "U", 2: "V"}
+
+
+class GbcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+class InvalidGraph(GbcError):
+    pass
+
+
+class CountOverflow(GbcError, ArithmeticError):
+    pass
+
+
+class CountTimeout(GbcError, TimeoutError):
+    pass
+
+
+class U128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+    def value(self) -> int:
+        return int(self.lo) | (int(self.hi) << 64)
+
+
+class CountOptions(ctypes.Structure):
+    _fields_ = [("anchor", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
+                ("enum_warps", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class CountInfo(ctypes.Structure):
+    _fields_ = [("anchor_used", ctypes.c_int32), ("set_size", ctypes.c_int32),
+                ("roots", ctypes.c_int64), ("candidates", ctypes.c_int64), ("units", ctypes.c_int64),
+                ("evals", ctypes.c_int64 * (MAX_PQ + 1)), ("passed", ctypes.c_int64 * (MAX_PQ + 1)),
+                ("words_r", ctypes.c_int64), ("words_l", ctypes.c_int64),
+                ("scratch_bytes", ctypes.c_int64),
+                ("ms_candidates", ctypes.c_float), ("ms_pairs", ctypes.c_float),
+                ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {
+            "anchor": _ANCHOR_NAMES.get(self.anchor_used, "?"),
+            "set_size": int(self.set_size),
+            "roots": int(self.roots),
+            "candidates": int(self.candidates),
+            "units": int(self.units),
+            "evals": [int(x) for x in self.evals],
+            "passed": [int(x) for x in self.passed],
+            "words_r": int(self.words_r),
+            "words_l": int(self.words_l),
+            "scratch_bytes": int(self.scratch_bytes),
+            "ms_candidates": float(self.ms_candidates),
+            "ms_pairs": float(self.ms_pairs),
+            "ms_enumerate": float(self.ms_enumerate),
+            "ms_total": float(self.ms_total),
+        }
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# name -> (restype, argtypes); the full C ABI of include/gbc.h
+_vp, _i32, _i64, _i32p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)
+SIGNATURES = {
+    "gbc_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "gbc_ctx_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "gbc_ctx_destroy": (None, [_vp]),
+    "gbc_load_graph": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "gbc_load_graph_device": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "gbc_free_graph": (None, [_vp]),
+    "gbc_graph_info": (ctypes.c_int, [_vp, _i32p, _i32p, ctypes.POINTER(_i64), _i32p, _i32p]),
+    "gbc_count": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128)]),
+    "gbc_count_ex": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(CountOptions),
+                                    ctypes.POINTER(U128), ctypes.POINTER(CountInfo)]),
+    "gbc_count_per_root": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(U128), ctypes.POINTER(U128)]),
+    "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gbc_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return LIB_PATH
+
+
+def load_library(path: str | None = None):
+    """Load libgbc.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libgbc.so not built ({p}); run paper_2403_07858_gb300.build()")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    """Compile libgbc.so for sm_103a if it is missing or stale; returns its path."""
+    import importlib
+    return importlib.import_module(__name__ + ".buildlib").build(force=force)
+
+
+def _check(status: int, what: str):
+    if status == GBC_OK:
+        return
+    lib = load_library()
+    msg = (lib.gbc_last_error() or b"").decode(errors="replace") or what
+    if status == GBC_ERR_INVALID_GRAPH:
+        raise InvalidGraph(status, msg)
+    if status == GBC_ERR_OVERFLOW:
+        raise CountOverflow(status, msg)
+    if status == GBC_ERR_TIMEOUT:
+        raise CountTimeout(status, msg)
+    raise GbcError(status, msg)
+
+
+def _ptr_host(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+class Graph:
+    """A graph resident on the device (freed by ``close`` or garbage collection)."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self._ctx = ctx
+        self._h = ctypes.c_void_p(handle)
+        n_u, n_v, mu, mv = _i32(), _i32(), _i32(), _i32()
+        n_e = _i64()
+        _check(load_library().gbc_graph_info(self._h, ctypes.byref(n_u), ctypes.byref(n_v), ctypes.byref(n_e),
+                                             ctypes.byref(mu), ctypes.byref(mv)), "gbc_graph_info")
+        self.n_u, self.n_v, self.n_edges = n_u.value, n_v.value, n_e.value
+        self.max_deg_u, self.max_deg_v = mu.value, mv.value
+
+    def close(self):
+        if self._h:
+            load_library().gbc_free_graph(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def count(self, p: int, q: int) -> int:
+        out = U128()
+        _check(load_library().gbc_count(self._h, p, q, ctypes.byref(out)), "gbc_count")
+        return out.value()
+
+    def count_ex(self, p: int, q: int, anchor: str = "auto", stats: bool = False,
+                 enum_warps: int = 0, time_limit_ms: int = 0) -> tuple[int, dict]:
+        opt = CountOptions()
+        opt.anchor = ANCHORS[anchor]
+        opt.collect_stats = 1 if stats else 0
+        opt.enum_warps = enum_warps
+        opt.time_limit_ms = time_limit_ms
+        out, info = U128(), CountInfo()
+        _check(load_library().gbc_count_ex(self._h, p, q, ctypes.byref(opt), ctypes.byref(out),
+                                           ctypes.byref(info)), "gbc_count_ex")
+        return out.value(), info.as_dict()
+
+    def count_per_root(self, p: int, q: int, anchor: str) -> tuple[int, list[int]]:
+        n_a = self.n_u if anchor == "U" else self.n_v
+        per = (U128 * max(1, n_a))()
+        tot = U128()
+        _check(load_library().gbc_count_per_root(self._h, p, q, ANCHORS[anchor], per, ctypes.byref(tot)),
+               "gbc_count_per_root")
+        return tot.value(), [per[i].value() for i in range(n_a)]
+
+
+class Context:
+    """One CUDA device, its stream and a device-memory budget for search scratch."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.gbc_ctx_create(device, mem_budget_bytes, ctypes.byref(h)), "gbc_ctx_create")
+        self._h = h
+        self.device = device
+
+    def set_stream(self, stream) -> None:
+        """Run later calls on ``stream`` (a torch.cuda.Stream, a raw handle, or None)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(load_library().gbc_ctx_set_stream(self._h, ctypes.c_void_p(handle or 0)), "gbc_ctx_set_stream")
+
+    def close(self):
+        if self._h:
+            load_library().gbc_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def load_graph(self, n_u: int, n_v: int, off_u, adj_u, off_v, adj_v) -> Graph:
+        lib = load_library()
+        h = ctypes.c_void_p()
+        arrays = (off_u, adj_u, off_v, adj_v)
+        if all(_is_cuda_tensor(x) for x in arrays):
+            ptrs = [ctypes.c_void_p(x.data_ptr()) for x in arrays]
+            _check(lib.gbc_load_graph_device(self._h, n_u, n_v, *ptrs, ctypes.byref(h)), "gbc_load_graph_device")
+        else:
+            keep = [_ptr_host(x) for x in arrays]
+            ptrs = [ctypes.c_void_p(p) for _, p in keep]
+            _check(lib.gbc_load_graph(self._h, n_u, n_v, *ptrs, ctypes.byref(h)), "gbc_load_graph")
+        return Graph(self, h.value)
+
+    def load(self, g) -> Graph:
+        """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""
+        return self.load_graph(g.n_u, g.n_v, g.off_u, g.adj_u, g.off_v, g.adj_v)

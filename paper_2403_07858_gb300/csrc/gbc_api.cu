@@ -1,0 +1,555 @@
+// Host side of the C ABI declared in include/gbc.h: contexts, graph loading
+// (validation and per-side index build on the device) and the count pipeline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gbc.h"
+#include "gbc_internal.cuh"
+
+using namespace gbc;
+
+// ---------------------------------------------------------------------------
+// errors
+static thread_local char t_err[512] = "";
+
+static gbc_status fail(gbc_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof t_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            gbc_status s_ = (e_ == cudaErrorMemoryAllocation) ? GBC_ERR_OOM : GBC_ERR_CUDA;   \
+            return fail(s_, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                     \
+    } while (0)
+
+struct gbc_ctx_s {
+    int device = 0;
+    size_t budget = 0;
+    int n_sms = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+    int live_graphs = 0;
+};
+
+struct gbc_graph_s {
+    gbc_ctx_s *ctx = nullptr;
+    int32_t nU = 0, nV = 0;
+    int64_t nE = 0;
+    int32_t *offU = nullptr, *adjU = nullptr, *offV = nullptr, *adjV = nullptr;
+    int32_t *degU = nullptr, *degV = nullptr;
+    int32_t *adjV_byU = nullptr, *mirrorU = nullptr;  // anchor U: V rows by U rank, U-edge mirrors
+    int32_t *adjU_byV = nullptr, *mirrorV = nullptr;  // anchor V
+    int32_t maxdegU = 0, maxdegV = 0;
+    unsigned long long wedgesU = 0, wedgesV = 0;      // sum C(deg, 2) on each side
+    ulonglong2 *binom = nullptr;
+    int32_t *n_ovf = nullptr;
+    int32_t binom_nmax = 0;
+};
+
+// Stream-ordered scratch that is released when the owner goes out of scope.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <typename T>
+    cudaError_t get(T **p, size_t n) {
+        size_t b = std::max<size_t>(n, 1) * sizeof(T);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(p), b, st);
+        if (e == cudaSuccess) { ptrs.push_back(*p); bytes += b; }
+        return e;
+    }
+};
+
+extern "C" {
+
+const char *gbc_status_string(gbc_status s) {
+    switch (s) {
+        case GBC_OK: return "ok";
+        case GBC_ERR_ARG: return "invalid argument";
+        case GBC_ERR_INVALID_GRAPH: return "invalid graph";
+        case GBC_ERR_OOM: return "out of device memory or budget";
+        case GBC_ERR_OVERFLOW: return "count exceeds 2^128-1";
+        case GBC_ERR_TIMEOUT: return "timeout";
+        case GBC_ERR_CUDA: return "CUDA error";
+        case GBC_PENDING: return "pending";
+        case GBC_ERR_REJECTED: return "rejected";
+    }
+    return "unknown status";
+}
+
+const char *gbc_last_error(void) { return t_err; }
+
+gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out) {
+    if (!out) return fail(GBC_ERR_ARG, "gbc_ctx_create: out is null");
+    int n = 0;
+    CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(GBC_ERR_ARG, "gbc_ctx_create: device %d of %d", device, n);
+    CK(cudaSetDevice(device));
+    gbc_ctx_s *c = new gbc_ctx_s();
+    c->device = device;
+    CK(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.8 * (double)free_b);
+    CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+    c->stream = c->own;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return GBC_OK;
+}
+
+gbc_status gbc_ctx_set_stream(gbc_ctx_t ctx, void *stream) {
+    if (!ctx) return fail(GBC_ERR_ARG, "gbc_ctx_set_stream: null context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->own;
+    return GBC_OK;
+}
+
+void gbc_ctx_destroy(gbc_ctx_t ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->own);
+    delete ctx;
+}
+
+void gbc_free_graph(gbc_graph_t g) {
+    if (!g) return;
+    cudaSetDevice(g->ctx->device);
+    cudaStream_t st = g->ctx->stream;
+    void *ps[] = {g->offU, g->adjU, g->offV, g->adjV, g->degU, g->degV, g->adjV_byU,
+                  g->mirrorU, g->adjU_byV, g->mirrorV, g->binom, g->n_ovf};
+    for (void *p : ps)
+        if (p) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    {
+        std::lock_guard<std::mutex> lk(g->ctx->mu);
+        g->ctx->live_graphs -= 1;
+    }
+    delete g;
+}
+
+gbc_status gbc_graph_info(gbc_graph_t g, int32_t *nU, int32_t *nV, int64_t *nE, int32_t *max_deg_u,
+                          int32_t *max_deg_v) {
+    if (!g) return fail(GBC_ERR_ARG, "gbc_graph_info: null graph");
+    if (nU) *nU = g->nU;
+    if (nV) *nV = g->nV;
+    if (nE) *nE = g->nE;
+    if (max_deg_u) *max_deg_u = g->maxdegU;
+    if (max_deg_v) *max_deg_v = g->maxdegV;
+    return GBC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// graph loading
+static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU,
+                              const int32_t *adjU, const int32_t *offV, const int32_t *adjV, bool host,
+                              gbc_graph_t *out) {
+    if (!ctx || !out || !offU || !offV) return fail(GBC_ERR_ARG, "gbc_load_graph: null argument");
+    if (nU < 0 || nV < 0) return fail(GBC_ERR_ARG, "gbc_load_graph: negative vertex count");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    // |E| from the ends of the two offset arrays
+    int32_t eU = 0, eV = 0;
+    if (host) {
+        eU = offU[nU];
+        eV = offV[nV];
+    } else {
+        CK(cudaMemcpyAsync(&eU, offU + nU, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&eV, offV + nV, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (eU < 0 || eU != eV)
+        return fail(GBC_ERR_INVALID_GRAPH, "gbc_load_graph: edge counts differ (U side %d, V side %d)", eU, eV);
+    if (eU > 0 && (!adjU || !adjV)) return fail(GBC_ERR_ARG, "gbc_load_graph: null adjacency");
+    gbc_graph_s *g = new gbc_graph_s();
+    g->ctx = ctx;
+    g->nU = nU;
+    g->nV = nV;
+    g->nE = eU;
+    auto cleanup = [&](gbc_status s) {
+        ctx->live_graphs += 1;  // gbc_free_graph decrements
+        ctx->mu.unlock();
+        gbc_free_graph(g);
+        ctx->mu.lock();
+        return s;
+    };
+#define CKG(expr)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return cleanup(fail(e_ == cudaErrorMemoryAllocation ? GBC_ERR_OOM : GBC_ERR_CUDA,      \
+                                "%s: %s", #expr, cudaGetErrorString(e_)));                          \
+    } while (0)
+    const size_t E = (size_t)g->nE;
+    CKG(cudaMallocAsync((void **)&g->offU, ((size_t)nU + 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->offV, ((size_t)nV + 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->adjU, std::max<size_t>(E, 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->adjV, std::max<size_t>(E, 1) * 4, st));
+    const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CKG(cudaMemcpyAsync(g->offU, offU, ((size_t)nU + 1) * 4, kind, st));
+    CKG(cudaMemcpyAsync(g->offV, offV, ((size_t)nV + 1) * 4, kind, st));
+    if (E) {
+        CKG(cudaMemcpyAsync(g->adjU, adjU, E * 4, kind, st));
+        CKG(cudaMemcpyAsync(g->adjV, adjV, E * 4, kind, st));
+    }
+    // validation: offsets first, then rows and the transpose relation
+    uint32_t *d_status = nullptr;
+    int32_t *d_small = nullptr;               // maxdegU, maxdegV
+    unsigned long long *d_wedges = nullptr;   // wedgesU, wedgesV
+    CKG(cudaMallocAsync((void **)&d_status, 4, st));
+    CKG(cudaMallocAsync((void **)&d_small, 8, st));
+    CKG(cudaMallocAsync((void **)&d_wedges, 16, st));
+    CKG(cudaMemsetAsync(d_status, 0, 4, st));
+    CKG(cudaMemsetAsync(d_small, 0, 8, st));
+    CKG(cudaMemsetAsync(d_wedges, 0, 16, st));
+    uint32_t h_status = 0;
+    CKG(launch_validate_offsets(g->offU, nU, g->nE, d_status, st));
+    CKG(launch_validate_offsets(g->offV, nV, g->nE, d_status, st));
+    CKG(cudaMemcpyAsync(&h_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+    CKG(cudaStreamSynchronize(st));
+    if (h_status == 0) {
+        CKG(launch_validate_rows(g->offU, g->adjU, nU, nV, d_status, st));
+        CKG(launch_validate_rows(g->offV, g->adjV, nV, nU, d_status, st));
+        CKG(cudaMemcpyAsync(&h_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        CKG(cudaStreamSynchronize(st));
+    }
+    if (h_status == 0) {
+        CKG(launch_validate_transpose(g->offU, g->adjU, nU, g->offV, g->adjV, d_status, st));
+        CKG(cudaMemcpyAsync(&h_status, d_status, 4, cudaMemcpyDeviceToHost, st));
+        CKG(cudaStreamSynchronize(st));
+    }
+    if (h_status != 0) {
+        cudaFreeAsync(d_status, st);
+        cudaFreeAsync(d_small, st);
+        cudaFreeAsync(d_wedges, st);
+        const char *why = (h_status & kStBadOffsets) ? "offsets not monotone or wrong ends"
+                          : (h_status & kStBadRange) ? "neighbour id out of range"
+                          : (h_status & kStUnsorted) ? "row not strictly increasing"
+                                                     : "V-side CSR is not the transpose of the U side";
+        return cleanup(fail(GBC_ERR_INVALID_GRAPH, "gbc_load_graph: %s", why));
+    }
+    // degrees, per-side rank-sorted rows and mirror positions
+    CKG(cudaMallocAsync((void **)&g->degU, std::max<size_t>(nU, 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->degV, std::max<size_t>(nV, 1) * 4, st));
+    CKG(launch_degrees(g->offU, nU, g->degU, d_small, d_wedges, st));
+    CKG(launch_degrees(g->offV, nV, g->degV, d_small + 1, d_wedges + 1, st));
+    int32_t h_small[2];
+    unsigned long long h_w[2];
+    CKG(cudaMemcpyAsync(h_small, d_small, 8, cudaMemcpyDeviceToHost, st));
+    CKG(cudaMemcpyAsync(h_w, d_wedges, 16, cudaMemcpyDeviceToHost, st));
+    CKG(cudaStreamSynchronize(st));
+    g->maxdegU = h_small[0];
+    g->maxdegV = h_small[1];
+    g->wedgesU = h_w[0];
+    g->wedgesV = h_w[1];
+    cudaFreeAsync(d_status, st);
+    cudaFreeAsync(d_small, st);
+    cudaFreeAsync(d_wedges, st);
+    CKG(cudaMallocAsync((void **)&g->adjV_byU, std::max<size_t>(E, 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->adjU_byV, std::max<size_t>(E, 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->mirrorU, std::max<size_t>(E, 1) * 4, st));
+    CKG(cudaMallocAsync((void **)&g->mirrorV, std::max<size_t>(E, 1) * 4, st));
+    {
+        int64_t *gtmp = nullptr;
+        const int32_t maxrow = std::max(g->maxdegU, g->maxdegV);
+        if (maxrow > 4096) {
+            int64_t P = 1;
+            while (P < maxrow) P <<= 1;
+            CKG(cudaMallocAsync((void **)&gtmp, (size_t)P * 8 * 64, st));
+        }
+        // anchor U: V rows sorted by U rank; anchor V: U rows sorted by V rank
+        CKG(launch_rank_sort_rows(g->offV, g->adjV, nV, g->degU, g->adjV_byU, g->maxdegV, gtmp, st));
+        CKG(launch_rank_sort_rows(g->offU, g->adjU, nU, g->degV, g->adjU_byV, g->maxdegU, gtmp, st));
+        if (gtmp) cudaFreeAsync(gtmp, st);
+    }
+    CKG(launch_mirror(g->offU, g->adjU, nU, g->offV, g->adjV_byU, g->degU, g->mirrorU, st));
+    CKG(launch_mirror(g->offV, g->adjV, nV, g->offU, g->adjU_byV, g->degV, g->mirrorV, st));
+    // binomial table up to the largest degree (|C_R| never exceeds it)
+    g->binom_nmax = std::max(std::max(g->maxdegU, g->maxdegV), 1);
+    CKG(cudaMallocAsync((void **)&g->binom, (size_t)(g->binom_nmax + 1) * (kMaxPQ + 1) * sizeof(ulonglong2), st));
+    CKG(cudaMallocAsync((void **)&g->n_ovf, (kMaxPQ + 1) * 4, st));
+    CKG(launch_binomial(g->binom, g->n_ovf, g->binom_nmax, st));
+    CKG(cudaStreamSynchronize(st));
+#undef CKG
+    ctx->live_graphs += 1;
+    *out = g;
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_load_graph(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU,
+                                     const int32_t *adjU, const int32_t *offV, const int32_t *adjV,
+                                     gbc_graph_t *out) {
+    return load_common(ctx, nU, nV, offU, adjU, offV, adjV, true, out);
+}
+
+extern "C" gbc_status gbc_load_graph_device(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU_d,
+                                            const int32_t *adjU_d, const int32_t *offV_d,
+                                            const int32_t *adjV_d, gbc_graph_t *out) {
+    return load_common(ctx, nU, nV, offU_d, adjU_d, offV_d, adjV_d, false, out);
+}
+
+// ---------------------------------------------------------------------------
+// the count pipeline
+static int pick_anchor(const gbc_graph_s *g, int p, int q) {
+    // A side of size 1 needs no search at all; otherwise enumerate the smaller
+    // set.  For p == q anchor the side with the lighter degree tail (smaller
+    // sum of C(deg, 2) over its own vertices): its roots have narrower C_R rows
+    // and fewer deep subtrees, which dominate the cost from p = q = 4 on.
+    if (p == 1) return GBC_ANCHOR_U;
+    if (q == 1) return GBC_ANCHOR_V;
+    if (p < q) return GBC_ANCHOR_U;
+    if (q < p) return GBC_ANCHOR_V;
+    return g->wedgesU <= g->wedgesV ? GBC_ANCHOR_U : GBC_ANCHOR_V;
+}
+
+struct Timer {
+    cudaEvent_t ev[5];
+    bool on = false;
+    void init(bool enable) {
+        on = enable;
+        if (on)
+            for (auto &e : ev) cudaEventCreate(&e);
+    }
+    void mark(int i, cudaStream_t st) {
+        if (on) cudaEventRecord(ev[i], st);
+    }
+    float between(int a, int b) {
+        float ms = 0.f;
+        if (on) cudaEventElapsedTime(&ms, ev[a], ev[b]);
+        return ms;
+    }
+    ~Timer() {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_options *opt, gbc_u128 *out,
+                             gbc_count_info *info, int force_anchor, unsigned long long *per_root_dev) {
+    if (!g || (!out && !per_root_dev)) return fail(GBC_ERR_ARG, "gbc_count: null argument");
+    if (p < 1 || q < 1 || p > GBC_MAX_PQ || q > GBC_MAX_PQ)
+        return fail(GBC_ERR_ARG, "gbc_count: p=%d q=%d outside [1, %d]", p, q, GBC_MAX_PQ);
+    gbc_ctx_s *ctx = g->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    gbc_count_info inf;
+    memset(&inf, 0, sizeof inf);
+    int anchor = force_anchor ? force_anchor : (opt && opt->anchor ? opt->anchor : pick_anchor(g, p, q));
+    if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_count: bad anchor %d", anchor);
+    const bool want_stats = opt && opt->collect_stats;
+
+    CountArgs a;
+    memset(&a, 0, sizeof a);
+    if (anchor == GBC_ANCHOR_U) {
+        a.g = SideView{g->nU, g->nV, g->offU, g->adjU, g->offV, g->adjV_byU, g->mirrorU, g->degU, g->maxdegU};
+        a.k = p;
+        a.kq = q;
+    } else {
+        a.g = SideView{g->nV, g->nU, g->offV, g->adjV, g->offU, g->adjU_byV, g->mirrorV, g->degV, g->maxdegV};
+        a.k = q;
+        a.kq = p;
+    }
+    a.binom = BinomTable{g->binom, g->n_ovf, g->binom_nmax};
+    inf.anchor_used = anchor;
+    inf.set_size = a.k;
+    gbc_u128 result{0, 0};
+
+    Timer tm;
+    tm.init(info != nullptr);
+    tm.mark(0, st);
+    Scratch sc(st);
+    // small device state: acc[2], status, tier_count[3], omega_max[3], queues[8], n_units, cand_max, totals[3]
+    struct Small {
+        unsigned long long acc[2];
+        int64_t totals[3];
+        uint32_t status;
+        int32_t tier_count[3];
+        int32_t omega_max[3];
+        int32_t queues[8];
+        int32_t n_units;
+        int32_t cand_max;
+        unsigned long long deadline;
+    };
+    Small *d_small = nullptr;
+    CK(sc.get(&d_small, 1));
+    CK(cudaMemsetAsync(d_small, 0, sizeof(Small), st));
+    SearchStats *d_stats = nullptr;
+    if (want_stats) {
+        CK(sc.get(&d_stats, 1));
+        CK(cudaMemsetAsync(d_stats, 0, sizeof(SearchStats), st));
+    }
+    a.acc = d_small->acc;
+    a.status = &d_small->status;
+    a.tier_count = d_small->tier_count;
+    a.omega_max = d_small->omega_max;
+    a.queues = d_small->queues;
+    a.n_units = &d_small->n_units;
+    a.cand_max = &d_small->cand_max;
+    a.deadline = &d_small->deadline;
+    if (opt && opt->time_limit_ms > 0)
+        CK(launch_set_deadline(a.deadline, (unsigned long long)opt->time_limit_ms * 1000000ull, st));
+    a.stats = d_stats;
+    a.per_root = per_root_dev;
+    Small h{};
+    const bool trivial = (a.k > a.g.nA) || (a.kq > a.g.maxdegA) || a.g.nA == 0;
+    if (!trivial) {
+        if (a.k == 1) {
+            CK(launch_single_vertex_sets(a, st));
+        } else {
+            const int64_t nA = a.g.nA;
+            CK(sc.get(&a.omega, nA));
+            CK(sc.get(&a.tier_list, 3 * nA));
+            CK(sc.get(&a.cand_count, nA));
+            CK(launch_root_omega(a, st));
+            CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            // tier-2 slabs: hash table of next_pow2(2*omega) slots + sort buffer
+            if (h.tier_count[2] > 0) {
+                if (h.omega_max[2] > (1 << 28))
+                    return fail(GBC_ERR_OOM, "gbc_count: a root has %d oriented wedges (limit 2^28)", h.omega_max[2]);
+                int64_t slots = 32, sortcap = 1;
+                while (slots < 2 * (int64_t)h.omega_max[2]) slots <<= 1;
+                while (sortcap < h.omega_max[2]) sortcap <<= 1;
+                a.slab_words = 2 * slots + 2 * sortcap;
+                const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
+                CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
+            }
+            CK(launch_candidates(a, false, h.tier_count, ctx->n_sms, st));
+            tm.mark(1, st);
+            if (a.k >= 3) {
+                int64_t *cand_off, *r_off, *s_off, *tmp;
+                CK(sc.get(&cand_off, nA + 1));
+                CK(sc.get(&r_off, nA + 1));
+                CK(sc.get(&s_off, nA + 1));
+                CK(sc.get(&tmp, 3 * ((nA + 1) / 2048 + 2)));
+                a.cand_off = cand_off;
+                a.r_off = r_off;
+                a.s_off = s_off;
+                CK(launch_root_offsets(a, cand_off, r_off, s_off, tmp, d_small->totals, st));
+                CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                a.n_cand = h.totals[0];
+                inf.candidates = h.totals[0];
+                if (a.n_cand >= INT32_MAX) return fail(GBC_ERR_OOM, "gbc_count: %lld candidates exceed one launch", (long long)a.n_cand);
+                const size_t need = (size_t)h.totals[0] * 12 + (size_t)h.totals[1] * 4 + (size_t)h.totals[2] * 4;
+                if (need + sc.bytes > ctx->budget)
+                    return fail(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need, ctx->budget);
+                if (a.n_cand > 0) {
+                    CK(sc.get(&a.cand, a.n_cand));
+                    CK(sc.get(&a.cand_root, a.n_cand));
+                    CK(sc.get(&a.R, h.totals[1]));
+                    CK(cudaMemsetAsync(a.R, 0, std::max<int64_t>(h.totals[1], 1) * 4, st));
+                    if (a.k >= 4) {
+                        CK(sc.get(&a.S, h.totals[2]));
+                        CK(cudaMemsetAsync(a.S, 0, std::max<int64_t>(h.totals[2], 1) * 4, st));
+                        CK(sc.get(&a.units, a.n_cand));
+                    }
+                    CK(launch_candidates(a, true, h.tier_count, ctx->n_sms, st));
+                    tm.mark(1, st);
+                    CK(launch_pairs(a, ctx->n_sms, st));
+                    tm.mark(2, st);
+                    if (a.k >= 4) {
+                        // stack layout from the largest row widths of this count
+                        const int max_wr = (a.g.maxdegA + 31) / 32;
+                        const int max_wl = (std::max(h.cand_max, 1) + 31) / 32;
+                        CK(launch_enumerate(a, opt ? opt->enum_warps : 0, max_wr, max_wl, ctx->n_sms, st));
+                    }
+                }
+            }
+            inf.scratch_bytes = (int64_t)sc.bytes;
+        }
+    }
+    tm.mark(3, st);
+    CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
+    SearchStats hs;
+    memset(&hs, 0, sizeof hs);
+    if (d_stats) CK(cudaMemcpyAsync(&hs, d_stats, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (h.status & kStTimeout) return fail(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its %d ms time limit", p, q,
+                                           opt ? opt->time_limit_ms : 0);
+    if (h.status & kStOverflow) return fail(GBC_ERR_OVERFLOW, "gbc_count: (%d,%d) count exceeds 2^128-1", p, q);
+    if (h.status) return fail(GBC_ERR_CUDA, "gbc_count: device status 0x%x", h.status);
+    result.lo = h.acc[0];
+    result.hi = h.acc[1];
+    if (info) {
+        inf.roots = (int64_t)hs.roots;
+        if (!inf.candidates) inf.candidates = (int64_t)hs.cands;
+        inf.units = want_stats ? (int64_t)hs.units : h.n_units;
+        for (int l = 0; l <= GBC_MAX_PQ; ++l) {
+            inf.evals[l] = (int64_t)hs.evals[l];
+            inf.passed[l] = (int64_t)hs.passed[l];
+        }
+        inf.words_r = (int64_t)hs.words_r;
+        inf.words_l = (int64_t)hs.words_l;
+        if (!trivial && a.k >= 2) {
+            inf.ms_candidates = tm.between(0, 1);
+            if (a.k >= 3 && a.n_cand > 0) {
+                inf.ms_pairs = tm.between(1, 2);
+                inf.ms_enumerate = a.k >= 4 ? tm.between(2, 3) : 0.f;
+            }
+        }
+        inf.ms_total = tm.between(0, 3);
+        *info = inf;
+    }
+    if (out) *out = result;
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_count(gbc_graph_t g, int p, int q, gbc_u128 *out) {
+    return count_impl(g, p, q, nullptr, out, nullptr, 0, nullptr);
+}
+
+extern "C" gbc_status gbc_count_ex(gbc_graph_t g, int p, int q, const gbc_count_options *opt, gbc_u128 *out,
+                                   gbc_count_info *info) {
+    gbc_u128 tmp;
+    return count_impl(g, p, q, opt, out ? out : &tmp, info, 0, nullptr);
+}
+
+extern "C" gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor, gbc_u128 *per_root,
+                                         gbc_u128 *total) {
+    if (!g || !per_root || !total) return fail(GBC_ERR_ARG, "gbc_count_per_root: null argument");
+    if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_count_per_root: anchor must be U or V");
+    const int64_t nA = anchor == GBC_ANCHOR_U ? g->nU : g->nV;
+    cudaStream_t st = g->ctx->stream;
+    CK(cudaSetDevice(g->ctx->device));
+    unsigned long long *d = nullptr;
+    CK(cudaMallocAsync((void **)&d, (size_t)std::max<int64_t>(nA, 1) * 16, st));
+    CK(cudaMemsetAsync(d, 0, (size_t)std::max<int64_t>(nA, 1) * 16, st));
+    gbc_status s = count_impl(g, p, q, nullptr, total, nullptr, anchor, d);
+    if (s == GBC_OK && nA > 0) {
+        cudaError_t e = cudaMemcpyAsync(per_root, d, (size_t)nA * 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = fail(GBC_ERR_CUDA, "gbc_count_per_root: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(d, st);
+    cudaStreamSynchronize(st);
+    return s;
+}

@@ -1,0 +1,213 @@
+// Internal declarations shared by the library's CUDA translation units.
+// Nothing here is part of the C ABI (see include/gbc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbc {
+
+constexpr int kMaxPQ = 16;
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+typedef unsigned __int128 u128;
+
+// Error bits of the device status word.
+enum : uint32_t {
+    kStOverflow = 1u << 0,      // a binomial term or the sum exceeded 2^128-1
+    kStScratch = 1u << 1,       // a scratch capacity bound was hit (host sizing bug)
+    kStBadOffsets = 1u << 2,    // validation: offsets not monotone / wrong ends
+    kStBadRange = 1u << 3,      // validation: neighbour id out of range
+    kStUnsorted = 1u << 4,      // validation: row not strictly increasing
+    kStNotTranspose = 1u << 5,  // validation: the two CSRs are not transposes
+    kStTimeout = 1u << 6,       // a bounded device wait ran out
+};
+
+// The graph seen from one anchor side A (the side whose vertices root the
+// search trees); O is the other side.  Vertex ids are the caller's ids.
+struct SideView {
+    int32_t nA, nO;
+    const int32_t *offA, *adjA;   // A -> O, rows sorted by O id
+    const int32_t *offO;          // O row offsets
+    const int32_t *adjO_rank;     // O -> A, rows sorted by A's rank key (deg, id)
+    const int32_t *mirror;        // per A-edge e = (a, o): index of a in adjO_rank row of o
+    const int32_t *degA;          // degree of every A vertex
+    int32_t maxdegA;
+};
+
+// Rank key of Def. 2 (reading: degree first, ties by id), ascending.
+__device__ __forceinline__ uint64_t rank_key(const int32_t *deg, int32_t a) {
+    return ((uint64_t)(uint32_t)deg[a] << 32) | (uint32_t)a;
+}
+
+// Binomial table of one graph: C(n, j) for 0 <= n <= nmax, 0 <= j <= 16, as
+// (lo, hi) pairs at [j * (nmax + 1) + n]; n_ovf[j] = least n with C(n, j) >
+// 2^128 - 1 (INT32_MAX if none up to nmax).  C(n, j) grows with n for j >= 1,
+// so the overflow test of a lookup is n >= n_ovf[j].
+struct BinomTable {
+    const ulonglong2 *c;
+    const int32_t *n_ovf;
+    int32_t nmax;
+};
+
+__device__ __forceinline__ ulonglong2 binom_lookup(const BinomTable &t, int j, int n, bool &ovf) {
+    if (n >= t.n_ovf[j]) { ovf = true; return make_ulonglong2(0, 0); }
+    return t.c[(size_t)j * (t.nmax + 1) + n];
+}
+
+__device__ __forceinline__ void add_u128(u128 &acc, ulonglong2 v, bool &ovf) {
+    u128 x = ((u128)v.y << 64) | v.x;
+    u128 s = acc + x;
+    if (s < acc) ovf = true;
+    acc = s;
+}
+
+__device__ __forceinline__ void add_u128(u128 &acc, u128 x, bool &ovf) {
+    u128 s = acc + x;
+    if (s < acc) ovf = true;
+    acc = s;
+}
+
+// Warp sum of a u128 with overflow detection; result valid in every lane.
+__device__ __forceinline__ u128 warp_sum_u128(u128 v, bool &ovf) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        uint64_t lo = __shfl_xor_sync(kFull, (uint64_t)v, o);
+        uint64_t hi = __shfl_xor_sync(kFull, (uint64_t)(v >> 64), o);
+        add_u128(v, ((u128)hi << 64) | lo, ovf);
+    }
+    ovf = __any_sync(kFull, ovf);
+    return v;
+}
+
+// Atomic 128-bit add into (lo, hi) with exact carry; sets kStOverflow in
+// *status when the running total passes 2^128 - 1.  All adds are non-negative,
+// so the total wraps exactly when some add carries out of hi.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *dst, u128 v, uint32_t *status) {
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    bool ovf = false;
+    if (lo) {
+        unsigned long long old = atomicAdd(dst, lo);
+        if (old + lo < old) { hi += 1; if (hi == 0) ovf = true; }
+    }
+    if (hi) {
+        unsigned long long old = atomicAdd(dst + 1, hi);
+        if (old + hi < old) ovf = true;
+    }
+    if (ovf) atomicOr(status, kStOverflow);
+}
+
+// Inclusive warp scan of an int.
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Per-count search statistics (filled only when stats are requested).
+struct SearchStats {
+    unsigned long long roots;
+    unsigned long long cands;
+    unsigned long long units;
+    unsigned long long evals[kMaxPQ + 1];
+    unsigned long long passed[kMaxPQ + 1];
+    unsigned long long words_r;
+    unsigned long long words_l;
+};
+
+// Everything one count's kernels share (device pointers).
+struct CountArgs {
+    SideView g;
+    BinomTable binom;
+    int k;          // |L| on the anchor side
+    int kq;         // |R| on the other side
+    // root classification
+    int32_t *omega;          // [nA] oriented wedge count of each root
+    int32_t *tier_list;      // 3 lists of roots, each of capacity nA
+    int32_t *tier_count;     // [3]
+    int32_t *omega_max;      // [3] max omega per tier
+    int32_t *queues;         // [8] persistent-grid work counters
+    // pass A / B outputs
+    int32_t *cand_count;     // [nA] |C_L| at each root (0 if filtered)
+    const int64_t *cand_off; // [nA+1] offsets into cand / cand_root
+    const int64_t *r_off;    // [nA+1] word offsets of each root's R block
+    const int64_t *s_off;    // [nA+1] word offsets of each root's S block
+    int32_t *cand;           // [sum c] candidate ids in rank order
+    int32_t *cand_root;      // [sum c] root of each candidate slot
+    uint32_t *R;             // R rows: row j of root r is W_R(r) words at R + r_off[r] + j*W_R
+    uint32_t *S;             // S rows: row j of root r is W_L(r) words at S + s_off[r] + j*W_L
+    int64_t n_cand;          // sum c
+    int32_t *units;          // live level-2 units (global candidate index)
+    int32_t *n_units;        // [1]
+    int32_t *cand_max;       // [1] largest |C_L| of a kept root
+    // global-tier hash slabs
+    int32_t *slab;           // per-CTA slabs for roots with large omega
+    int64_t slab_words;      // int32 words per CTA slab
+    // results
+    unsigned long long *acc;        // [2] (lo, hi)
+    unsigned long long *per_root;   // [2*nA] or null
+    uint32_t *status;
+    SearchStats *stats;             // or null
+    unsigned long long *deadline;   // [1] globaltimer (ns) past which kernels stop; 0 = none
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// True when the count's deadline has passed (then kStTimeout is set) or another
+// warp already flagged a timeout.
+__device__ __forceinline__ bool past_deadline(const CountArgs &a) {
+    if (*(volatile uint32_t *)a.status & kStTimeout) return true;
+    const unsigned long long d = *(volatile unsigned long long *)a.deadline;
+    if (d != 0ull && global_ns() > d) {
+        atomicOr(a.status, kStTimeout);
+        return true;
+    }
+    return false;
+}
+
+// Tier bounds on omega (exact number of oriented wedges of a root).
+constexpr int kWarpTierOmega = 256;    // warp per root, shared-memory table of 512 slots
+constexpr int kWarpTierSlots = 512;
+constexpr int kCtaTierOmega = 4096;    // CTA per root, shared-memory table of 8192 slots
+constexpr int kCtaTierSlots = 8192;
+constexpr int kCtaThreads = 256;
+constexpr int kWarpTierWarps = 8;
+constexpr int kWarpTierBytes = 2 * kWarpTierSlots * 4 + kWarpTierOmega * 8;
+
+// Launchers (gbc_kernels.cu).  All run on `st`; none synchronises.
+cudaError_t launch_validate_offsets(const int32_t *off, int32_t n, int64_t nE, uint32_t *status, cudaStream_t st);
+cudaError_t launch_validate_rows(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other,
+                                 uint32_t *status, cudaStream_t st);
+cudaError_t launch_validate_transpose(const int32_t *offU, const int32_t *adjU, int32_t nU,
+                                      const int32_t *offV, const int32_t *adjV, uint32_t *status,
+                                      cudaStream_t st);
+cudaError_t launch_degrees(const int32_t *off, int32_t n, int32_t *deg, int32_t *maxdeg,
+                           unsigned long long *wedges, cudaStream_t st);
+cudaError_t launch_rank_sort_rows(const int32_t *off, const int32_t *adj, int32_t n_rows,
+                                  const int32_t *deg_target, int32_t *out, int32_t max_row,
+                                  int64_t *gtmp, cudaStream_t st);
+cudaError_t launch_mirror(const int32_t *offA, const int32_t *adjA, int32_t nA, const int32_t *offO,
+                          const int32_t *adjO_rank, const int32_t *degA, int32_t *mirror, cudaStream_t st);
+cudaError_t launch_binomial(ulonglong2 *c, int32_t *n_ovf, int32_t nmax, cudaStream_t st);
+
+cudaError_t launch_single_vertex_sets(const CountArgs &a, cudaStream_t st);
+cudaError_t launch_set_deadline(unsigned long long *deadline, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t launch_root_omega(const CountArgs &a, cudaStream_t st);
+cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tier_counts_host,
+                              int n_sms, cudaStream_t st);
+cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *r_off, int64_t *s_off,
+                                int64_t *tmp, int64_t *totals, cudaStream_t st);
+cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st);
+cudaError_t launch_enumerate(const CountArgs &a, int n_warps, int max_wr, int max_wl, int n_sms,
+                             cudaStream_t st);
+
+}  // namespace gbc

@@ -1,0 +1,799 @@
+// Per-count kernels: 2-hop candidates and their C_R bitmap rows, pairwise C_L
+// rows, the enumeration of the search trees, and the u128 reduction.
+//
+// Notation (Sec. III-A, Alg. 1): anchor side A, other side O; k = |L| on A,
+// kq = |R| on O.  Root u (an A vertex) with d = |N(u)| keeps
+//   C_L(u) = { w in A ranked above u : |N(u) & N(w)| >= kq }   (c = |C_L(u)|)
+// in rank order, and for each candidate j the row R_j, a d-bit bitmap over the
+// positions of N(u) (bit i set when N(u)[i] is a neighbour of candidate j).
+// For k >= 4 it also keeps S_j, a c-bit bitmap with bit x (x > j) set when
+// candidates j and x share >= kq neighbours inside N(u) (the q-strength 2-hop
+// relation of Sec. II, taken inside the root's neighbourhood).
+#include <algorithm>
+
+#include "gbc_internal.cuh"
+
+namespace gbc {
+
+// ---------------------------------------------------------------------------
+// k == 1: every anchor vertex alone is L; it contributes C(deg, kq).
+__global__ void k_single_vertex_sets(CountArgs a) {
+    u128 acc = 0;
+    bool ovf = false;
+    const int64_t n = a.g.nA;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((n + 31) / 32) * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) {
+            bool o = false;
+            ulonglong2 v = binom_lookup(a.binom, a.kq, a.g.degA[i], o);
+            if (a.per_root) {
+                a.per_root[2 * i] = v.x;
+                a.per_root[2 * i + 1] = v.y;
+            }
+            ovf |= o;
+            add_u128(acc, v, ovf);
+        }
+    }
+    acc = warp_sum_u128(acc, ovf);
+    if ((threadIdx.x & 31) == 0) {
+        if (ovf) atomicOr(a.status, kStOverflow);
+        atomic_add_u128(a.acc, acc, a.status);
+    }
+    if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats->roots, (unsigned long long)n);
+}
+
+__global__ void k_set_deadline(unsigned long long *deadline, unsigned long long limit_ns) {
+    *deadline = limit_ns ? global_ns() + limit_ns : 0ull;
+}
+
+cudaError_t launch_set_deadline(unsigned long long *deadline, unsigned long long limit_ns, cudaStream_t st) {
+    k_set_deadline<<<1, 1, 0, st>>>(deadline, limit_ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_single_vertex_sets(const CountArgs &a, cudaStream_t st) {
+    int grid = (int)std::min<int64_t>(((int64_t)a.g.nA + 255) / 256 + 1, 2048);
+    k_single_vertex_sets<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Oriented wedge count of each root and its tier.  omega(u) counts wedges
+// u - v - w with w ranked above u; a root can hold at most omega/kq candidates,
+// so roots with omega < (k-1)*kq cannot reach |L| = k and are dropped
+// (Alg. 1 root filter, applied before the candidates are even formed).
+__global__ void k_root_omega(CountArgs a) {
+    const SideView &g = a.g;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < g.nA; u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t om = 0;
+        const int32_t d = g.degA[u];
+        a.cand_count[u] = 0;
+        if (d >= a.kq) {
+            for (int32_t e = g.offA[u]; e < g.offA[u + 1]; ++e) {
+                const int32_t o = g.adjA[e];
+                om += (int64_t)(g.offO[o + 1] - g.offO[o] - g.mirror[e] - 1);
+            }
+        }
+        a.omega[u] = (int32_t)om;
+        if (om >= (int64_t)(a.k - 1) * a.kq && om > 0) {
+            const int tier = om <= kWarpTierOmega ? 0 : (om <= kCtaTierOmega ? 1 : 2);
+            const int slot = atomicAdd(&a.tier_count[tier], 1);
+            a.tier_list[(int64_t)tier * g.nA + slot] = (int32_t)u;
+            atomicMax(&a.omega_max[tier], (int32_t)om);
+        }
+    }
+}
+
+cudaError_t launch_root_omega(const CountArgs &a, cudaStream_t st) {
+    int grid = (int)std::min<int64_t>(((int64_t)a.g.nA + 255) / 256, 4096);
+    if (grid == 0) return cudaSuccess;
+    k_root_omega<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Candidate generation for one root by a group of NW warps (NW = 1: a warp;
+// otherwise the whole CTA).  The wedges u - N(u)[i] - w (w ranked above u) are
+// the suffixes of the rank-sorted rows of N(u)'s members; they are counted in
+// an open-addressing hash table keyed by w.
+template <int NW>
+struct Group {
+    __device__ static int tid() { return NW == 1 ? (threadIdx.x & 31) : threadIdx.x; }
+    __device__ static int size() { return 32 * NW; }
+    __device__ static int warp() { return NW == 1 ? 0 : (threadIdx.x >> 5); }
+    __device__ static void sync() {
+        if (NW == 1) __syncwarp(); else __syncthreads();
+    }
+};
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t w, int log2slots) {
+    return ((uint32_t)w * 2654435761u) >> (32 - log2slots);
+}
+
+// Linear probing; a table is sized to at least twice the number of wedges of
+// its root, so a probe sequence never wraps.  The probe count is bounded all
+// the same: running past it flags kStScratch instead of spinning.
+__device__ __forceinline__ void table_insert(int32_t *keys, int32_t *vals, int log2slots, int32_t w,
+                                             uint32_t *status) {
+    const uint32_t mask = (1u << log2slots) - 1;
+    uint32_t h = hash_slot(w, log2slots);
+    for (uint32_t probes = 0; probes <= mask; ++probes) {
+        int32_t k = keys[h];
+        if (k == -1) {
+            k = atomicCAS(&keys[h], -1, w);
+            if (k == -1) k = w;
+        }
+        if (k == w) { atomicAdd(&vals[h], 1); return; }
+        h = (h + 1) & mask;
+    }
+    atomicOr(status, kStScratch);
+}
+
+// Slot of w (present by construction); returns -1 and flags kStScratch if not found.
+__device__ __forceinline__ int32_t table_find(const int32_t *keys, int log2slots, int32_t w, uint32_t *status) {
+    const uint32_t mask = (1u << log2slots) - 1;
+    uint32_t h = hash_slot(w, log2slots);
+    for (uint32_t probes = 0; probes <= mask; ++probes) {
+        if (keys[h] == w) return (int32_t)h;
+        h = (h + 1) & mask;
+    }
+    atomicOr(status, kStScratch);
+    return -1;
+}
+
+// Visit every oriented wedge (w, i) of root u: i = position in N(u), w in the
+// part of N(N(u)[i]) ranked above u.  Each warp of the group takes chunks of 32
+// positions; the warp's lanes share the chunk's wedges evenly through a scan.
+template <int NW, typename F>
+__device__ __forceinline__ void for_each_wedge(const SideView &g, int32_t u, F fn) {
+    const int lane = threadIdx.x & 31;
+    const int32_t d = g.degA[u];
+    const int32_t eA = g.offA[u];
+    for (int32_t base = Group<NW>::warp() * 32; base < d; base += 32 * NW) {
+        const int32_t i = base + lane;
+        int32_t len = 0, s0 = 0;
+        if (i < d) {
+            const int32_t e = eA + i;
+            const int32_t o = g.adjA[e];
+            s0 = g.offO[o] + g.mirror[e] + 1;
+            len = g.offO[o + 1] - s0;
+        }
+        const int32_t incl = warp_incl_scan(len);
+        const int32_t total = __shfl_sync(kFull, incl, 31);
+        for (int32_t f0 = 0; f0 < total; f0 += 32) {
+            const int32_t f = f0 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1) {
+                const int32_t v = __shfl_sync(kFull, incl, owner + b - 1);
+                if (v <= f) owner += b;
+            }
+            owner = min(owner, 31);
+            const int32_t o_incl = __shfl_sync(kFull, incl, owner);
+            const int32_t o_len = __shfl_sync(kFull, len, owner);
+            const int32_t o_s0 = __shfl_sync(kFull, s0, owner);
+            if (f < total) fn(g.adjO_rank[o_s0 + (f - (o_incl - o_len))], base + owner);
+        }
+    }
+}
+
+template <typename Ptr>
+__device__ void group_bitonic_u64(Ptr keys, int P, int tid, int gsize, bool cta) {
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += gsize) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t x = keys[i], y = keys[ixj];
+                    bool asc = (i & k) == 0;
+                    if ((x > y) == asc) { keys[i] = y; keys[ixj] = x; }
+                }
+            }
+            if (cta) __syncthreads(); else __syncwarp();
+        }
+    }
+}
+
+// One root, pass A (BUILD = false): count candidates; for k == 2 the leaves
+// are the candidates themselves and their C(common, kq) are summed here.
+// Pass B (BUILD = true): list the candidates in rank order and set their R rows.
+template <int NW, bool BUILD>
+__device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32_t *vals,
+                             uint64_t *sortbuf, int32_t *shared_int, u128 &acc, bool &ovf) {
+    typedef Group<NW> G;
+    const SideView &g = a.g;
+    const int tid = G::tid(), gs = G::size();
+    const int32_t om = a.omega[u];
+    int log2slots = 5;
+    while ((1 << log2slots) < 2 * om) ++log2slots;
+    const int slots = 1 << log2slots;
+    for (int s = tid; s < slots; s += gs) { keys[s] = -1; vals[s] = 0; }
+    G::sync();
+    for_each_wedge<NW>(g, u, [&](int32_t w, int32_t) { table_insert(keys, vals, log2slots, w, a.status); });
+    G::sync();
+    const int32_t d = g.degA[u];
+    const int32_t WR = (d + 31) >> 5;
+    if (!BUILD) {
+        int c = 0;
+        u128 leaf = 0;
+        bool o = false;
+        for (int s = tid; s < slots; s += gs) {
+            if (keys[s] >= 0 && vals[s] >= a.kq) {
+                ++c;
+                if (a.k == 2) add_u128(leaf, binom_lookup(a.binom, a.kq, vals[s], o), o);
+            }
+        }
+        // group reductions through the warp sums and (for CTAs) shared memory
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(kFull, c, off);
+        if (a.k == 2) leaf = warp_sum_u128(leaf, o);
+        if (NW > 1) {
+            if (tid == 0) shared_int[0] = 0;
+            __syncthreads();
+            if ((tid & 31) == 0) atomicAdd(&shared_int[0], c);
+            __syncthreads();
+            c = shared_int[0];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            a.cand_count[u] = c;
+            if (c >= a.k - 1) {
+                atomicMax(a.cand_max, c);
+                if (a.stats) {
+                    atomicAdd(&a.stats->roots, 1ull);
+                    atomicAdd(&a.stats->cands, (unsigned long long)c);
+                    if (a.k == 2) {
+                        atomicAdd(&a.stats->evals[2], (unsigned long long)c);
+                        atomicAdd(&a.stats->passed[2], (unsigned long long)c);
+                        atomicAdd(&a.stats->words_r, (unsigned long long)c * WR);
+                    }
+                }
+            }
+        }
+        if (a.k == 2 && (tid & 31) == 0) {
+            // each warp adds its own part (a warp group has one warp)
+            if (o) atomicOr(a.status, kStOverflow);
+            if (a.per_root) atomic_add_u128(a.per_root + 2 * (int64_t)u, leaf, a.status);
+            add_u128(acc, leaf, ovf);
+        }
+        G::sync();
+        return;
+    }
+    // ---- pass B
+    const int32_t c = a.cand_count[u];
+    if (tid == 0) shared_int[0] = 0;
+    G::sync();
+    for (int s = tid; s < slots; s += gs) {
+        if (keys[s] >= 0 && vals[s] >= a.kq) {
+            int idx = atomicAdd(&shared_int[0], 1);
+            sortbuf[idx] = rank_key(g.degA, keys[s]);
+        }
+    }
+    G::sync();
+    int P = 1;
+    while (P < c) P <<= 1;
+    for (int i = c + tid; i < P; i += gs) sortbuf[i] = ~0ull;
+    G::sync();
+    group_bitonic_u64(sortbuf, P, tid, gs, NW > 1);
+    const int64_t coff = a.cand_off[u];
+    for (int i = tid; i < c; i += gs) {
+        const int32_t w = (int32_t)(uint32_t)sortbuf[i];
+        a.cand[coff + i] = w;
+        a.cand_root[coff + i] = u;
+        const int32_t slot = table_find(keys, log2slots, w, a.status);
+        if (slot >= 0) vals[slot] = -1 - i;
+    }
+    G::sync();
+    uint32_t *Rb = a.R + a.r_off[u];
+    for_each_wedge<NW>(g, u, [&](int32_t w, int32_t i) {
+        const int32_t slot = table_find(keys, log2slots, w, a.status);
+        const int32_t v = slot >= 0 ? vals[slot] : 0;
+        if (v < 0) atomicOr(&Rb[(int64_t)(-1 - v) * WR + (i >> 5)], 1u << (i & 31));
+    });
+    G::sync();
+}
+
+// Tier 0: one warp per root; each warp owns a 512-slot table in shared memory.
+template <bool BUILD>
+__global__ void __launch_bounds__(32 * kWarpTierWarps)
+k_cand_warp(CountArgs a) {
+    // per warp: keys[512] | vals[512] | sort[256] (u64); plus 2 ints per warp
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ int32_t s_int[kWarpTierWarps][2];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *mine = dyn + (size_t)w * kWarpTierBytes;
+    int32_t *my_keys = reinterpret_cast<int32_t *>(mine);
+    int32_t *my_vals = my_keys + kWarpTierSlots;
+    uint64_t *my_sort = reinterpret_cast<uint64_t *>(my_vals + kWarpTierSlots);
+    u128 acc = 0;
+    bool ovf = false;
+    const int n = a.tier_count[0];
+    int32_t *queue = a.queues + (BUILD ? 3 : 0);
+    while (true) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(queue, 1);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= n || past_deadline(a)) break;
+        const int32_t u = a.tier_list[idx];
+        if (BUILD && a.cand_count[u] < a.k - 1) continue;
+        process_root<1, BUILD>(a, u, my_keys, my_vals, my_sort, s_int[w], acc, ovf);
+    }
+    if (!BUILD && a.k == 2 && lane == 0) {
+        if (ovf) atomicOr(a.status, kStOverflow);
+        atomic_add_u128(a.acc, acc, a.status);
+    }
+}
+
+// Tiers 1 and 2: one CTA per root, table in dynamic shared memory (tier 1) or
+// in the CTA's global slab (tier 2).
+template <bool BUILD, bool GLOBAL_TABLE>
+__global__ void __launch_bounds__(kCtaThreads)
+k_cand_cta(CountArgs a) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ int32_t s_int[2];
+    __shared__ int32_t s_idx;
+    const int tier = GLOBAL_TABLE ? 2 : 1;
+    int32_t *keys, *vals;
+    uint64_t *sortbuf;
+    if (GLOBAL_TABLE) {
+        int32_t *slab = a.slab + (int64_t)blockIdx.x * a.slab_words;
+        int slots = 32;
+        while (slots < 2 * a.omega_max[2]) slots <<= 1;
+        keys = slab;
+        vals = slab + slots;
+        sortbuf = reinterpret_cast<uint64_t *>(slab + 2 * (int64_t)slots);
+    } else {
+        keys = reinterpret_cast<int32_t *>(dyn);
+        vals = keys + kCtaTierSlots;
+        sortbuf = reinterpret_cast<uint64_t *>(vals + kCtaTierSlots);
+    }
+    u128 acc = 0;
+    bool ovf = false;
+    const int n = a.tier_count[tier];
+    int32_t *queue = a.queues + (BUILD ? 3 : 0) + tier;
+    while (true) {
+        if (threadIdx.x == 0) s_idx = past_deadline(a) ? n : atomicAdd(queue, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= n) break;
+        const int32_t u = a.tier_list[(int64_t)tier * a.g.nA + idx];
+        if (BUILD && a.cand_count[u] < a.k - 1) continue;
+        process_root<kCtaThreads / 32, BUILD>(a, u, keys, vals, sortbuf, s_int, acc, ovf);
+    }
+    if (!BUILD && a.k == 2 && (threadIdx.x & 31) == 0) {
+        if (ovf) atomicOr(a.status, kStOverflow);
+        atomic_add_u128(a.acc, acc, a.status);
+    }
+}
+
+constexpr size_t kCtaTierSmem = 2 * kCtaTierSlots * sizeof(int32_t) + kCtaTierOmega * sizeof(uint64_t);
+
+cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tier_counts_host,
+                              int n_sms, cudaStream_t st) {
+    constexpr int warp_smem = kWarpTierWarps * kWarpTierBytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_cand_cta<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaTierSmem);
+        cudaFuncSetAttribute(k_cand_cta<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaTierSmem);
+        cudaFuncSetAttribute(k_cand_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+        cudaFuncSetAttribute(k_cand_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+        attr_set = true;
+    }
+    if (tier_counts_host[0] > 0) {
+        int grid = std::min(n_sms * 4, (tier_counts_host[0] + kWarpTierWarps - 1) / kWarpTierWarps);
+        if (build) k_cand_warp<true><<<grid, 32 * kWarpTierWarps, warp_smem, st>>>(a);
+        else k_cand_warp<false><<<grid, 32 * kWarpTierWarps, warp_smem, st>>>(a);
+    }
+    if (tier_counts_host[1] > 0) {
+        int grid = std::min(n_sms * 2, tier_counts_host[1]);
+        if (build) k_cand_cta<true, false><<<grid, kCtaThreads, kCtaTierSmem, st>>>(a);
+        else k_cand_cta<false, false><<<grid, kCtaThreads, kCtaTierSmem, st>>>(a);
+    }
+    if (tier_counts_host[2] > 0) {
+        int grid = std::min(n_sms * 2, tier_counts_host[2]);
+        if (build) k_cand_cta<true, true><<<grid, kCtaThreads, 0, st>>>(a);
+        else k_cand_cta<false, true><<<grid, kCtaThreads, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-root offsets: exclusive scans of c', c'*W_R and c'*W_L, where c' = c for
+// roots that keep >= k-1 candidates and 0 otherwise.  Three-phase block scan.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ void root_sizes(const CountArgs &a, int64_t r, int64_t &c, int64_t &wr, int64_t &wl) {
+    c = 0; wr = 0; wl = 0;
+    if (r >= a.g.nA) return;
+    const int32_t cc = a.cand_count[r];
+    if (cc < a.k - 1 || cc == 0) return;
+    c = cc;
+    wr = (int64_t)cc * ((a.g.degA[r] + 31) >> 5);
+    wl = a.k >= 4 ? (int64_t)cc * ((cc + 31) >> 5) : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *tmp, T &total) {
+    // tmp: kScanThreads/32 entries
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) tmp[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        T x = lane < kScanThreads / 32 ? tmp[lane] : 0;
+        T xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(kFull, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < kScanThreads / 32) tmp[lane] = xi - x;
+        if (lane == kScanThreads / 32 - 1) tmp[kScanThreads / 32] = xi;
+    }
+    __syncthreads();
+    T res = incl - v + tmp[w];
+    total = tmp[kScanThreads / 32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(CountArgs a, int64_t *tile_sums) {
+    __shared__ int64_t tmp[3][kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int64_t s[3] = {0, 0, 0};
+    for (int t = 0; t < kScanItems; ++t) {
+        int64_t c, wr, wl;
+        root_sizes(a, base + t, c, wr, wl);
+        s[0] += c; s[1] += wr; s[2] += wl;
+    }
+    for (int m = 0; m < 3; ++m) {
+        int64_t tot;
+        block_excl_scan(s[m], tmp[m], tot);
+        if (threadIdx.x == 0) tile_sums[(int64_t)m * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int64_t *tile_sums, int n_tiles, int64_t *totals) {
+    __shared__ int64_t tmp[kScanThreads / 32 + 1];
+    for (int m = 0; m < 3; ++m) {
+        int64_t carry = 0;
+        for (int b0 = 0; b0 < n_tiles; b0 += kScanThreads) {
+            const int b = b0 + threadIdx.x;
+            int64_t v = b < n_tiles ? tile_sums[(int64_t)m * n_tiles + b] : 0;
+            int64_t tot;
+            int64_t ex = block_excl_scan(v, tmp, tot);
+            if (b < n_tiles) tile_sums[(int64_t)m * n_tiles + b] = carry + ex;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) totals[m] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(CountArgs a, const int64_t *tile_sums, int64_t *cand_off, int64_t *r_off, int64_t *s_off) {
+    __shared__ int64_t tmp[3][kScanThreads / 32 + 1];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int64_t v[3][kScanItems];
+    int64_t s[3] = {0, 0, 0};
+    for (int t = 0; t < kScanItems; ++t) {
+        root_sizes(a, base + t, v[0][t], v[1][t], v[2][t]);
+        s[0] += v[0][t]; s[1] += v[1][t]; s[2] += v[2][t];
+    }
+    int64_t *outs[3] = {cand_off, r_off, s_off};
+    for (int m = 0; m < 3; ++m) {
+        int64_t tot;
+        int64_t ex = block_excl_scan(s[m], tmp[m], tot) + tile_sums[(int64_t)m * gridDim.x + blockIdx.x];
+        for (int t = 0; t < kScanItems; ++t) {
+            const int64_t r = base + t;
+            if (r <= a.g.nA) outs[m][r] = ex;
+            ex += v[m][t];
+        }
+    }
+}
+
+cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *r_off, int64_t *s_off,
+                                int64_t *tmp, int64_t *totals, cudaStream_t st) {
+    // covers r in [0, nA] (the entry nA receives the total)
+    const int n_tiles = (int)(((int64_t)a.g.nA + 1 + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<n_tiles, kScanThreads, 0, st>>>(a, tmp);
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(tmp, n_tiles, totals);
+    k_scan_apply<<<n_tiles, kScanThreads, 0, st>>>(a, tmp, cand_off, r_off, s_off);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Level-2 rows.  Warp per candidate j of a root: for every later candidate x,
+// n = popc(R_j & R_x).  k == 3: (u, j, x) is a leaf and adds C(n, kq) when
+// n >= kq.  k >= 4: the ballot of (n >= kq) over 32 consecutive x is word
+// x/32 of S_j; units with |S_j| >= k-2 go to the enumeration list.
+template <bool STATS>
+__global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
+    const int lane = threadIdx.x & 31;
+    u128 acc = 0;
+    bool ovf = false;
+    while (true) {
+        int64_t gidx = 0;
+        if (lane == 0) gidx = atomicAdd(a.queues + 6, 1);
+        gidx = __shfl_sync(kFull, gidx, 0);
+        if (gidx >= a.n_cand || past_deadline(a)) break;
+        const int32_t r = a.cand_root[gidx];
+        const int32_t j = (int32_t)(gidx - a.cand_off[r]);
+        const int32_t c = a.cand_count[r];
+        const int32_t WR = (a.g.degA[r] + 31) >> 5;
+        const int32_t WL = (c + 31) >> 5;
+        const uint32_t *Rb = a.R + a.r_off[r];
+        const uint32_t *Rj = Rb + (int64_t)j * WR;
+        u128 row_acc = 0;
+        int passes = 0;
+        for (int32_t t = (j + 1) >> 5; t < WL; ++t) {
+            const int32_t x = (t << 5) + lane;
+            const bool valid = x > j && x < c;
+            int n = 0;
+            if (valid) {
+                const uint32_t *Rx = Rb + (int64_t)x * WR;
+                for (int32_t w = 0; w < WR; ++w) n += __popc(Rj[w] & Rx[w]);
+            }
+            const bool pass = valid && n >= a.kq;
+            const unsigned m = __ballot_sync(kFull, pass);
+            passes += __popc(m);
+            if (a.k == 3) {
+                if (pass) add_u128(row_acc, binom_lookup(a.binom, a.kq, n, ovf), ovf);
+            } else if (lane == 0) {
+                a.S[a.s_off[r] + (int64_t)j * WL + t] = m;
+            }
+        }
+        if (a.k >= 4 && lane == 0 && passes >= a.k - 2) {
+            const int slot = atomicAdd(a.n_units, 1);
+            a.units[slot] = (int32_t)gidx;
+        }
+        if (a.per_root && a.k == 3) {
+            row_acc = warp_sum_u128(row_acc, ovf);
+            if (lane == 0) atomic_add_u128(a.per_root + 2 * (int64_t)r, row_acc, a.status);
+            if (lane != 0) row_acc = 0;
+        }
+        add_u128(acc, row_acc, ovf);
+        if (STATS && lane == 0) {
+            atomicAdd(&a.stats->evals[2], 1ull);
+            atomicAdd(&a.stats->passed[2], 1ull);
+            atomicAdd(&a.stats->words_r, (unsigned long long)WR);
+            atomicAdd(&a.stats->words_l, (unsigned long long)WL);
+            if (a.k == 3) {
+                atomicAdd(&a.stats->evals[3], (unsigned long long)passes);
+                atomicAdd(&a.stats->passed[3], (unsigned long long)passes);
+                atomicAdd(&a.stats->words_r, (unsigned long long)passes * WR);
+            } else if (passes >= a.k - 2) {
+                atomicAdd(&a.stats->units, 1ull);
+            }
+        }
+    }
+    if (a.k == 3) {
+        acc = warp_sum_u128(acc, ovf);
+        if (lane == 0) {
+            if (ovf) atomicOr(a.status, kStOverflow);
+            atomic_add_u128(a.acc, acc, a.status);
+        }
+    }
+}
+
+cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
+    if (a.n_cand == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((a.n_cand + 7) / 8, (int64_t)n_sms * 8);
+    if (a.stats) k_pairs<true><<<grid, 256, 0, st>>>(a);
+    else k_pairs<false><<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Enumeration of the subtrees below the live level-2 units (k >= 4).
+//
+// A warp owns one unit at a time and walks its subtree depth-first.  At each
+// node the warp takes the node's children 32 at a time (the next 32 set bits of
+// C_L) and evaluates them side by side, one child per lane, against the
+// parent's C_R and C_L, which sit in shared memory and are read by every lane
+// at once (the siblings-share-the-parent idea of Sec. IV's hybrid search).
+// Children at the last level are leaves and add C(|C_R'|, kq); the others that
+// pass both pruning tests (|C_R'| >= kq, |C_L'| >= k - |L'|) are entered one by
+// one, their C_R' and C_L' rebuilt cooperatively (lanes over words).
+//
+// Per warp, for each level lv = |L| - 2 in [0, k-2):
+//   CR[lv] : WRmax words, CL[lv] : WLmax words, xs[lv] : 32 child ids,
+//   cursor[lv] (next C_L position to take), dmask[lv] (children still to enter).
+struct EnumLayout {
+    int wr, wl;     // row capacities in words
+    int levels;     // k - 2
+    __host__ __device__ int level_words() const { return wr + wl + 32; }
+    __host__ __device__ int warp_words() const { return levels * level_words() + 2 * kMaxPQ; }
+};
+
+// The next <= 32 set bits of CL at or after *cursor, in order, into xs.
+__device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c, int &cursor, int32_t *xs) {
+    const int lane = threadIdx.x & 31;
+    int got = 0;
+    int pos = cursor;
+    while (got < 32 && pos < c) {
+        const int w0 = pos >> 5;
+        const int wi = w0 + lane;
+        uint32_t word = wi < WL ? CL[wi] : 0u;
+        if (lane == 0) word &= ~0u << (pos & 31);
+        const int cnt = __popc(word);
+        const int incl = warp_incl_scan(cnt);
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int need = 32 - got;
+        const int take = min(cnt, max(0, need - excl));
+        uint32_t wv = word;
+        int last = 0;
+        for (int b = 0; b < take; ++b) {
+            const int bit = __ffs(wv) - 1;
+            wv &= wv - 1;
+            xs[got + excl + b] = (wi << 5) + bit;
+            last = (wi << 5) + bit;
+        }
+        if (total <= need) {
+            got += total;
+            pos = (w0 + 32) << 5;
+        } else {
+            const int holder = __ffs(__ballot_sync(kFull, incl >= need)) - 1;
+            pos = __shfl_sync(kFull, last, holder) + 1;
+            got = 32;
+        }
+    }
+    cursor = pos;
+    __syncwarp();
+    return got;
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(256)
+k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
+    extern __shared__ __align__(16) uint32_t smem_stack[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    uint32_t *base = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
+                            : smem_stack + (int64_t)wib * lay.warp_words();
+    int32_t *cursor = reinterpret_cast<int32_t *>(base + lay.levels * lay.level_words());
+    uint32_t *dmask = reinterpret_cast<uint32_t *>(cursor + kMaxPQ);
+    auto CR = [&](int lv) { return base + (int64_t)lv * lay.level_words(); };
+    auto CL = [&](int lv) { return base + (int64_t)lv * lay.level_words() + lay.wr; };
+    auto XS = [&](int lv) { return reinterpret_cast<int32_t *>(base + (int64_t)lv * lay.level_words() + lay.wr + lay.wl); };
+
+    const int k = a.k, kq = a.kq;
+    u128 acc = 0;
+    bool ovf = false;
+    const int n_units = *a.n_units;
+    while (true) {
+        int uidx = 0;
+        if (lane == 0) uidx = atomicAdd(a.queues + 7, 1);
+        uidx = __shfl_sync(kFull, uidx, 0);
+        if (uidx >= n_units || past_deadline(a)) break;
+        const int64_t gidx = a.units[uidx];
+        const int32_t r = a.cand_root[gidx];
+        const int32_t j = (int32_t)(gidx - a.cand_off[r]);
+        const int32_t c = a.cand_count[r];
+        const int32_t WR = (a.g.degA[r] + 31) >> 5;
+        const int32_t WL = (c + 31) >> 5;
+        const uint32_t *Rb = a.R + a.r_off[r];
+        const uint32_t *Sb = a.S + a.s_off[r];
+        u128 unit_acc = 0;
+        // level 2 node {u, j}: C_R = R_j, C_L = S_j
+        for (int w = lane; w < WR; w += 32) CR(0)[w] = Rb[(int64_t)j * WR + w];
+        for (int w = lane; w < WL; w += 32) CL(0)[w] = Sb[(int64_t)j * WL + w];
+        if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; }
+        __syncwarp();
+        int lv = 0;
+        unsigned batches = 0;
+        while (true) {
+            if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
+            const uint32_t dm = dmask[lv];
+            if (dm != 0) {
+                const int t = __ffs(dm) - 1;
+                const int32_t x = XS(lv)[t];
+                __syncwarp();
+                if (lane == 0) dmask[lv] = dm & (dm - 1);
+                const uint32_t *cr = CR(lv), *cl = CL(lv);
+                uint32_t *cr2 = CR(lv + 1), *cl2 = CL(lv + 1);
+                const uint32_t *Rx = Rb + (int64_t)x * WR, *Sx = Sb + (int64_t)x * WL;
+                const int w0 = (x + 1) >> 5;
+                for (int w = lane; w < WR; w += 32) cr2[w] = cr[w] & Rx[w];
+                for (int w = lane; w < WL; w += 32) cl2[w] = w >= w0 ? (cl[w] & Sx[w]) : 0u;
+                if (lane == 0) { cursor[lv + 1] = x + 1; dmask[lv + 1] = 0; }
+                __syncwarp();
+                ++lv;
+                continue;
+            }
+            int cur = cursor[lv];
+            const int got = gather_children(CL(lv), WL, c, cur, XS(lv));
+            if (lane == 0) cursor[lv] = cur;
+            if (got == 0) {
+                __syncwarp();
+                if (lv == 0) break;
+                --lv;
+                continue;
+            }
+            const int ell = lv + 2;          // |L| of the node
+            const bool leaf = (ell + 1 == k);
+            const uint32_t *cr = CR(lv), *cl = CL(lv);
+            int n = 0;
+            int32_t x = 0;
+            if (lane < got) {
+                x = XS(lv)[lane];
+                const uint32_t *Rx = Rb + (int64_t)x * WR;
+                for (int w = 0; w < WR; ++w) n += __popc(cr[w] & Rx[w]);
+            }
+            const bool pass = lane < got && n >= kq;
+            bool desc = false;
+            if (leaf) {
+                if (pass) add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
+            } else if (pass) {
+                const uint32_t *Sx = Sb + (int64_t)x * WL;
+                int m = 0;
+                for (int w = (x + 1) >> 5; w < WL; ++w) m += __popc(cl[w] & Sx[w]);
+                desc = m >= k - (ell + 1);
+            }
+            const unsigned dmb = __ballot_sync(kFull, desc);
+            if (STATS) {
+                const unsigned pm = __ballot_sync(kFull, pass);
+                if (lane == 0) {
+                    atomicAdd(&a.stats->evals[ell + 1], (unsigned long long)got);
+                    atomicAdd(&a.stats->passed[ell + 1], (unsigned long long)__popc(pm));
+                    atomicAdd(&a.stats->words_r, (unsigned long long)got * WR);
+                    if (!leaf) atomicAdd(&a.stats->words_l, (unsigned long long)__popc(pm) * WL);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) dmask[lv] = dmb;
+            __syncwarp();
+        }
+        if (a.per_root) {
+            u128 s = warp_sum_u128(unit_acc, ovf);
+            if (lane == 0) atomic_add_u128(a.per_root + 2 * (int64_t)r, s, a.status);
+        }
+        add_u128(acc, unit_acc, ovf);
+    }
+    acc = warp_sum_u128(acc, ovf);
+    if (lane == 0) {
+        if (ovf) atomicOr(a.status, kStOverflow);
+        atomic_add_u128(a.acc, acc, a.status);
+    }
+}
+
+cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, int max_wl, int n_sms,
+                             cudaStream_t st) {
+    EnumLayout lay{max_wr, max_wl, a.k - 2};
+    const size_t per_warp = (size_t)lay.warp_words() * 4;
+    const int warps_per_cta = 8;
+    const size_t smem = per_warp * warps_per_cta;
+    const bool use_smem = smem <= 160 * 1024;
+    int grid = n_sms * 4;
+    if (n_warps_hint > 0) grid = max(1, n_warps_hint / warps_per_cta);
+    uint32_t *gstack = nullptr;
+    cudaError_t err;
+    if (use_smem) {
+        auto kern = a.stats ? k_enumerate<true> : k_enumerate<false>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_cta, smem);
+        if (n_warps_hint <= 0) grid = n_sms * max(1, per_sm);
+        kern<<<grid, 32 * warps_per_cta, smem, st>>>(a, lay, nullptr);
+    } else {
+        err = cudaMallocAsync(reinterpret_cast<void **>(&gstack), per_warp * warps_per_cta * grid, st);
+        if (err != cudaSuccess) return err;
+        if (a.stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
+        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
+        err = cudaGetLastError();
+        cudaFreeAsync(gstack, st);
+        return err;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbc
