@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark: time per exact (p,q)-biclique count on one GB300.
+
+Workload: the Chung-Lu power-law bipartite graph of seed 2 (|U| = 200k,
+|V| = 100k, |E| = 2M, degree exponents 2.0 on U and 2.3 on V, int32 CSR on both
+sides), counted for p = q in {2, 3, 4, 5, 6}.  One step is that whole sweep
+(five counts, every stage of the search on the device).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbc|reference]
+
+Prints one JSON line.  value = device time per count with the graph already
+resident in HBM (CUDA events on the library's stream, max over ranks);
+e2e = the same through the public API from pinned host CSR arrays (load,
+copy, validate, index, count, read back) per step.  --impl reference times
+the CPU oracle on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): every rank counts its own replica of the sweep (weak
+scaling); only a barrier and the max-time reduction cross ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import bipgen  # noqa: E402
+
+WORKLOAD = ("chung-lu seed 2: |U|=200000 |V|=100000 |E|=2000000, exponents 2.0 (U) / 2.3 (V), "
+            "int32 CSR both sides; sweep p=q in {2,3,4,5,6}")
+METRIC = "time per (p,q) count"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbc", choices=["gbc", "reference"])
+    ap.add_argument("--pq", default="2,3,4,5,6", help="p = q values of one step")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline leg and the reference arm).
+def _oracle_worker(q_out, graph_args, anchor, k, roots):
+    sys.path.insert(0, ROOT)
+    import oracle
+    g = bipgen.chung_lu(*graph_args)
+    oracle.build()
+    for r in roots:
+        t0 = time.perf_counter()
+        oracle.count(g, k, k, anchor=anchor, roots=(r, r + 1))
+        q_out.put((r, time.perf_counter() - t0))
+    q_out.put(None)
+
+
+def oracle_sample(pqs, anchors, budget_s, seed):
+    """Time the oracle on seeded uniform samples of roots, one (p,q) after the
+    other, each for budget_s / len(pqs) seconds; extrapolate to all roots."""
+    graph_args = (2, 200_000, 100_000, 2_000_000, 2.0, 2.3)
+    n_roots = {"U": 200_000, "V": 100_000}
+    ctx = mp.get_context("spawn")
+    per = budget_s / len(pqs)
+    est_s, detail = 0.0, []
+    for k, anchor in zip(pqs, anchors):
+        rng = __import__("numpy").random.default_rng(seed + k)
+        roots = rng.permutation(n_roots[anchor])[:100_000].tolist()
+        q = ctx.Queue()
+        proc = ctx.Process(target=_oracle_worker, args=(q, graph_args, anchor, k, roots), daemon=True)
+        proc.start()
+        # the child first regenerates the graph; its timing starts at the first root
+        done, spent, t_first = 0, 0.0, None
+        t_start = time.perf_counter()
+        deadline = None
+        while True:
+            # before the first root arrives: graph generation (a few s) plus the budget
+            timeout = (t_start + 60.0 + per if deadline is None else deadline) - time.perf_counter()
+            try:
+                item = q.get(timeout=max(0.0, timeout))
+            except Exception:
+                if t_first is None:
+                    t_first = t_start + 60.0
+                break
+            if item is None:
+                break
+            if t_first is None:
+                t_first = time.perf_counter() - item[1]
+                deadline = t_first + per
+            done += 1
+            spent += item[1]
+            if time.perf_counter() >= deadline:
+                break
+        in_flight = proc.is_alive()
+        proc.kill()
+        proc.join()
+        wall = (time.perf_counter() - t_first) if t_first else 0.0
+        denom = done + (1 if in_flight else 0)
+        est = max(wall, spent) * n_roots[anchor] / max(1, denom)
+        est_s += est
+        detail.append(f"p=q={k} anchor {anchor}: {done} roots in {max(wall, spent):.1f} s")
+    return est_s, detail
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pqs = [int(x) for x in args.pq.split(",")]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reference_arm(args, pqs)
+        return
+
+    import torch
+    import paper_2403_07858_gb300 as gbc
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    gbc.build()
+
+    g = bipgen.workload_powerlaw_2m()
+    sha = bipgen.graph_sha256(g)
+    ctx = gbc.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident graph: counts, then warm-up and timed sweeps
+    h = ctx.load(g)
+    ref_counts, anchors = {}, {}
+    for k in pqs:
+        n, info = h.count_ex(k, k)
+        ref_counts[k], anchors[k] = n, info["anchor"]
+    for _ in range(args.warmup):
+        for k in pqs:
+            assert h.count(k, k) == ref_counts[k]
+    step_ms, enum_ms, enum_words, enum_launches, launches = [], 0.0, 0, 0, 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush outside the timed region
+            barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = []
+            for k in pqs:
+                n, info = h.count_ex(k, k)
+                assert n == ref_counts[k]
+                infos.append(info)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            step_ms.append(e0.elapsed_time(e1))
+            for info in infos:
+                launches += info["launches"]
+                if info["enum_words"] > 0:
+                    enum_ms += info["ms_enumerate"]
+                    enum_words += info["enum_words"]
+                    enum_launches += 1
+    clocks = clk.summary()
+    h.close()
+    ms_step = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    n_counts = len(pqs) * world
+    value = ms_step / n_counts  # whole job: every rank's counts in the max-over-ranks step time
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(x).pin_memory() for x in (g.off_u, g.adj_u, g.off_v, g.adj_v)]
+        host = [x.numpy() for x in pinned]
+        h2d = sum(int(x.nbytes) for x in host)
+        e2e_ms = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hh = ctx.load_graph(g.n_u, g.n_v, *host)
+            for k in pqs:
+                assert hh.count(k, k) == ref_counts[k]
+            hh.close()
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            barrier()
+        em = statistics.mean(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([em], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            em = float(t.item())
+        e2e = {"value": em / n_counts, "unit": "ms", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 16 * len(pqs)}
+
+    # ---- roofline of the dominant kernel (the enumeration) against measured HBM
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    roof = None
+    if enum_launches:
+        bytes_per_launch = 4.0 * enum_words / enum_launches
+        ms_per_launch = enum_ms / enum_launches
+        achieved = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+        peak = hbm if hbm else 6800.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _ncu_traffic(), "kernel": "k_enumerate",
+                "peak_source": "measured" if hbm else "fallback",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_per_launch}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est_s, detail = oracle_sample(pqs, [anchors[k] for k in pqs], args.cpu_budget, seed=7)
+        cpu = {"value": est_s * 1e3 / len(pqs), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": "seeded uniform sample of roots per (p,q), per-root oracle time scaled by "
+                         "(all roots / sampled roots); " + "; ".join(detail)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bitmaps, u128 counts", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph_sha256": sha, "counts_per_step": len(pqs),
+                       "anchor": {str(k): anchors[k] for k in pqs},
+                       "l2": "512 MiB written between timed steps (outside the events); per-count "
+                             "scratch also exceeds L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "counts": {str(k): str(ref_counts[k]) for k in pqs},
+            "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _ncu_traffic():
+    """dram bytes per launch of the enumeration kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "enumerate_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2403_07858_gb300", "csrc", "gbc_search.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch_scaled")
+
+
+def _auto_anchor(g, k):
+    """The library's anchor rule for p = q = k: the side whose own degrees give
+    the smaller sum of C(deg, 2) (the oracle counts the same from either side)."""
+    import numpy as np
+    du = np.diff(g.off_u).astype(np.int64)
+    dv = np.diff(g.off_v).astype(np.int64)
+    if k == 1:
+        return "U"
+    return "U" if int((du * (du - 1) // 2).sum()) <= int((dv * (dv - 1) // 2).sum()) else "V"
+
+
+def reference_arm(args, pqs):
+    """The oracle timed on this host's cores, each step a bounded sample."""
+    g = bipgen.workload_powerlaw_2m()
+    anchors = [_auto_anchor(g, k) for k in pqs]
+    times = []
+    detail = []
+    budget = min(args.cpu_budget, 12.0)
+    for _ in range(args.warmup):
+        oracle_sample(pqs[:1], anchors[:1], 1.0, seed=3)
+    for s in range(args.steps):
+        est_s, detail = oracle_sample(pqs, anchors, budget, seed=11 + s)
+        times.append(est_s * 1e3 / len(pqs))
+    v = statistics.mean(times)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * len(pqs), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u128 (CPU oracle)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "counts_per_step": len(pqs)},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": "per step: seeded uniform sample of roots per (p,q), scaled to all roots; "
+                                   + "; ".join(detail)},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,10 @@ typedef struct {
     float ms_pairs;             /* device time: pairwise rows (C_L bitmaps) */
     float ms_enumerate;         /* device time: enumeration kernel */
     float ms_total;             /* device time of the whole count */
+    int64_t enum_words;         /* C_R + C_L words of the children the enumeration kernel
+                                   evaluated (its algorithmic work; always filled) */
+    int32_t launches;           /* CUDA kernels this count launched */
+    int32_t reserved_i;
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */

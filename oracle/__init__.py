@@ -41,6 +41,7 @@ class OracleStats(ctypes.Structure):
         ("words_r", ctypes.c_int64),
         ("words_l", ctypes.c_int64),
         ("cand_total", ctypes.c_int64),
+        ("words_lvl2", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -51,6 +52,7 @@ class OracleStats(ctypes.Structure):
             "words_r": int(self.words_r),
             "words_l": int(self.words_l),
             "cand_total": int(self.cand_total),
+            "words_lvl2": int(self.words_lvl2),
         }
 
 

@@ -55,6 +55,8 @@ typedef struct {
     int64_t words_r;                  /* C_R words read                           */
     int64_t words_l;                  /* C_L words read                           */
     int64_t cand_total;               /* sum over roots of |C_L| at the root      */
+    int64_t words_lvl2;               /* the part of words_r + words_l read by the
+                                         children of the roots (|L| = 2)          */
 } orc_stats;
 
 /* ---- binomial coefficients by Pascal's rule, checked ---------------------- */
@@ -160,6 +162,7 @@ static void expand(tree_t *t, int ell, const int32_t *cr, int ncr, const int32_t
         int n_cr = intersect(cr, ncr, t->rsets[x], t->rlen[x], cr_next);
         t->st.evals[ell + 1] += 1;
         t->st.words_r += t->wr;
+        if (ell == 1) t->st.words_lvl2 += t->wr;
         if (n_cr < g->q) continue;
         t->st.passed[ell + 1] += 1;
         if (ell + 1 == g->p) {
@@ -173,6 +176,7 @@ static void expand(tree_t *t, int ell, const int32_t *cr, int ncr, const int32_t
             if (t->compat[(size_t)x * t->c + y]) cl_next[n_cl++] = y;
         }
         t->st.words_l += t->wl;
+        if (ell == 1) t->st.words_lvl2 += t->wl;
         if (n_cl < g->p - (ell + 1)) continue;
         expand(t, ell + 1, cr_next, n_cr, cl_next, n_cl);
     }
@@ -251,6 +255,7 @@ static int count_root(const view_t *g, int32_t u, u128 *out, int *ovf, orc_stats
     for (int l = 0; l <= ORC_MAXK; ++l) { st->evals[l] += t.st.evals[l]; st->passed[l] += t.st.passed[l]; }
     st->words_r += t.st.words_r;
     st->words_l += t.st.words_l;
+    st->words_lvl2 += t.st.words_lvl2;
 done:
     if (t.rsets) for (int i = 0; i < c; ++i) free(t.rsets[i]);
     free(t.rsets); free(t.rlen); free(t.compat); free(t.scratch); free(t.clbuf); free(cl0);

@@ -69,7 +69,8 @@ class CountInfo(ctypes.Structure):
                 ("words_r", ctypes.c_int64), ("words_l", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64),
                 ("ms_candidates", ctypes.c_float), ("ms_pairs", ctypes.c_float),
-                ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {
@@ -87,6 +88,8 @@ class CountInfo(ctypes.Structure):
             "ms_pairs": float(self.ms_pairs),
             "ms_enumerate": float(self.ms_enumerate),
             "ms_total": float(self.ms_total),
+            "enum_words": int(self.enum_words),
+            "launches": int(self.launches),
         }
 
 

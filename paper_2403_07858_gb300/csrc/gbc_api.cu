@@ -381,6 +381,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
     inf.set_size = a.k;
     gbc_u128 result{0, 0};
 
+    t_launches = 0;
     Timer tm;
     tm.init(info != nullptr);
     tm.mark(0, st);
@@ -396,6 +397,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         int32_t n_units;
         int32_t cand_max;
         unsigned long long deadline;
+        unsigned long long enum_words;
     };
     Small *d_small = nullptr;
     CK(sc.get(&d_small, 1));
@@ -413,6 +415,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
     a.n_units = &d_small->n_units;
     a.cand_max = &d_small->cand_max;
     a.deadline = &d_small->deadline;
+    a.enum_words = &d_small->enum_words;
     if (opt && opt->time_limit_ms > 0)
         CK(launch_set_deadline(a.deadline, (unsigned long long)opt->time_limit_ms * 1000000ull, st));
     a.stats = d_stats;
@@ -517,6 +520,8 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
             }
         }
         inf.ms_total = tm.between(0, 3);
+        inf.enum_words = (int64_t)h.enum_words;
+        inf.launches = t_launches;
         *info = inf;
     }
     if (out) *out = result;

@@ -120,6 +120,10 @@ struct SearchStats {
     unsigned long long words_l;
 };
 
+// Kernels launched by the calling thread since the last reset (a count runs on
+// the calling thread, serialised per context).
+extern thread_local int t_launches;
+
 // Everything one count's kernels share (device pointers).
 struct CountArgs {
     SideView g;
@@ -154,6 +158,7 @@ struct CountArgs {
     uint32_t *status;
     SearchStats *stats;             // or null
     unsigned long long *deadline;   // [1] globaltimer (ns) past which kernels stop; 0 = none
+    unsigned long long *enum_words; // [1] C_R + C_L words read by the enumeration kernel
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {

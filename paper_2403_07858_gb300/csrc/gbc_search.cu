@@ -15,6 +15,8 @@
 
 namespace gbc {
 
+thread_local int t_launches = 0;
+
 // ---------------------------------------------------------------------------
 // k == 1: every anchor vertex alone is L; it contributes C(deg, kq).
 __global__ void k_single_vertex_sets(CountArgs a) {
@@ -54,6 +56,7 @@ cudaError_t launch_set_deadline(unsigned long long *deadline, unsigned long long
 cudaError_t launch_single_vertex_sets(const CountArgs &a, cudaStream_t st) {
     int grid = (int)std::min<int64_t>(((int64_t)a.g.nA + 255) / 256 + 1, 2048);
     k_single_vertex_sets<<<grid, 256, 0, st>>>(a);
+    ++t_launches;
     return cudaGetLastError();
 }
 
@@ -88,6 +91,7 @@ cudaError_t launch_root_omega(const CountArgs &a, cudaStream_t st) {
     int grid = (int)std::min<int64_t>(((int64_t)a.g.nA + 255) / 256, 4096);
     if (grid == 0) return cudaSuccess;
     k_root_omega<<<grid, 256, 0, st>>>(a);
+    ++t_launches;
     return cudaGetLastError();
 }
 
@@ -384,16 +388,19 @@ cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tie
         int grid = std::min(n_sms * 4, (tier_counts_host[0] + kWarpTierWarps - 1) / kWarpTierWarps);
         if (build) k_cand_warp<true><<<grid, 32 * kWarpTierWarps, warp_smem, st>>>(a);
         else k_cand_warp<false><<<grid, 32 * kWarpTierWarps, warp_smem, st>>>(a);
+        ++t_launches;
     }
     if (tier_counts_host[1] > 0) {
         int grid = std::min(n_sms * 2, tier_counts_host[1]);
         if (build) k_cand_cta<true, false><<<grid, kCtaThreads, kCtaTierSmem, st>>>(a);
         else k_cand_cta<false, false><<<grid, kCtaThreads, kCtaTierSmem, st>>>(a);
+        ++t_launches;
     }
     if (tier_counts_host[2] > 0) {
         int grid = std::min(n_sms * 2, tier_counts_host[2]);
         if (build) k_cand_cta<true, true><<<grid, kCtaThreads, 0, st>>>(a);
         else k_cand_cta<false, true><<<grid, kCtaThreads, 0, st>>>(a);
+        ++t_launches;
     }
     return cudaGetLastError();
 }
@@ -506,6 +513,7 @@ cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *
     k_scan_reduce<<<n_tiles, kScanThreads, 0, st>>>(a, tmp);
     k_scan_tiles<<<1, kScanThreads, 0, st>>>(tmp, n_tiles, totals);
     k_scan_apply<<<n_tiles, kScanThreads, 0, st>>>(a, tmp, cand_off, r_off, s_off);
+    t_launches += 3;
     return cudaGetLastError();
 }
 
@@ -588,6 +596,7 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>((a.n_cand + 7) / 8, (int64_t)n_sms * 8);
     if (a.stats) k_pairs<true><<<grid, 256, 0, st>>>(a);
     else k_pairs<false><<<grid, 256, 0, st>>>(a);
+    ++t_launches;
     return cudaGetLastError();
 }
 
@@ -668,6 +677,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     const int k = a.k, kq = a.kq;
     u128 acc = 0;
     bool ovf = false;
+    unsigned long long words = 0;  // C_R + C_L words of the evaluated children (algorithmic work)
     const int n_units = *a.n_units;
     while (true) {
         int uidx = 0;
@@ -739,6 +749,8 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
                 desc = m >= k - (ell + 1);
             }
             const unsigned dmb = __ballot_sync(kFull, desc);
+            words += (unsigned long long)got * WR;
+            if (!leaf) words += (unsigned long long)__popc(__ballot_sync(kFull, pass)) * WL;
             if (STATS) {
                 const unsigned pm = __ballot_sync(kFull, pass);
                 if (lane == 0) {
@@ -746,6 +758,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
                     atomicAdd(&a.stats->passed[ell + 1], (unsigned long long)__popc(pm));
                     atomicAdd(&a.stats->words_r, (unsigned long long)got * WR);
                     if (!leaf) atomicAdd(&a.stats->words_l, (unsigned long long)__popc(pm) * WL);
+
                 }
             }
             __syncwarp();
@@ -762,6 +775,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     if (lane == 0) {
         if (ovf) atomicOr(a.status, kStOverflow);
         atomic_add_u128(a.acc, acc, a.status);
+        atomicAdd(a.enum_words, words);
     }
 }
 
@@ -784,11 +798,13 @@ cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, i
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_cta, smem);
         if (n_warps_hint <= 0) grid = n_sms * max(1, per_sm);
         kern<<<grid, 32 * warps_per_cta, smem, st>>>(a, lay, nullptr);
+        ++t_launches;
     } else {
         err = cudaMallocAsync(reinterpret_cast<void **>(&gstack), per_warp * warps_per_cta * grid, st);
         if (err != cudaSuccess) return err;
         if (a.stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
         else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
+        ++t_launches;
         err = cudaGetLastError();
         cudaFreeAsync(gstack, st);
         return err;
