@@ -104,9 +104,12 @@ def test_tree_statistics_match_oracle(gpu_ctx, p, q, anchor):
     assert info["passed"] == st["passed"]
     assert info["words_r"] == st["words_r"]
     assert info["words_l"] == st["words_l"]
-    if p >= 4 or (anchor == "V" and q >= 4):
+    k = p if anchor == "U" else q  # size of the set enumerated on the anchor side
+    if k >= 4:
         # the enumeration kernel walks the levels below the root's children
         assert info["enum_words"] == st["words_r"] + st["words_l"] - st["words_lvl2"]
+    else:
+        assert info["enum_words"] == 0
     assert info["launches"] > 0
     h.close()
 
