@@ -465,6 +465,10 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
                 if (need + sc.bytes > ctx->budget)
                     return fail(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need, ctx->budget);
                 if (a.n_cand > 0) {
+                    const int64_t nE = std::max<int64_t>(g->nE, 1);
+                    CK(sc.get(&a.poscnt, nE));
+                    CK(sc.get(&a.posmap, nE));
+                    CK(cudaMemsetAsync(a.poscnt, 0, (size_t)nE * 4, st));
                     CK(sc.get(&a.cand, a.n_cand));
                     CK(sc.get(&a.cand_root, a.n_cand));
                     CK(sc.get(&a.R, h.totals[1]));
@@ -480,7 +484,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
                     tm.mark(2, st);
                     if (a.k >= 4) {
                         // stack layout from the largest row widths of this count
-                        const int max_wr = (a.g.maxdegA + 31) / 32;
+                        const int max_wr = row_stride(a.g.maxdegA);
                         const int max_wl = (std::max(h.cand_max, 1) + 31) / 32;
                         CK(launch_enumerate(a, opt ? opt->enum_warps : 0, max_wr, max_wl, ctx->n_sms, st));
                     }

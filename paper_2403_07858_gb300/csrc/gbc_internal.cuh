@@ -159,7 +159,13 @@ struct CountArgs {
     SearchStats *stats;             // or null
     unsigned long long *deadline;   // [1] globaltimer (ns) past which kernels stop; 0 = none
     unsigned long long *enum_words; // [1] C_R + C_L words read by the enumeration kernel
+    int32_t *poscnt;                // [|E|] per anchor edge slot: candidates containing that position
+    int32_t *posmap;                // [|E|] per anchor edge slot: its bit position in the R rows
 };
+
+// R rows of a root with d neighbours take ceil(d/32) words, stored with an even
+// stride so that two words load at once.
+__host__ __device__ __forceinline__ int32_t row_stride(int32_t d) { return (((d + 31) >> 5) + 1) & ~1; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;

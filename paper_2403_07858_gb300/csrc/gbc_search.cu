@@ -122,7 +122,7 @@ __device__ __forceinline__ void table_insert(int32_t *keys, int32_t *vals, int l
     const uint32_t mask = (1u << log2slots) - 1;
     uint32_t h = hash_slot(w, log2slots);
     for (uint32_t probes = 0; probes <= mask; ++probes) {
-        int32_t k = keys[h];
+        int32_t k = ((volatile int32_t *)keys)[h];
         if (k == -1) {
             k = atomicCAS(&keys[h], -1, w);
             if (k == -1) k = w;
@@ -138,7 +138,7 @@ __device__ __forceinline__ int32_t table_find(const int32_t *keys, int log2slots
     const uint32_t mask = (1u << log2slots) - 1;
     uint32_t h = hash_slot(w, log2slots);
     for (uint32_t probes = 0; probes <= mask; ++probes) {
-        if (keys[h] == w) return (int32_t)h;
+        if (((volatile const int32_t *)keys)[h] == w) return (int32_t)h;
         h = (h + 1) & mask;
     }
     atomicOr(status, kStScratch);
@@ -221,10 +221,12 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
         int c = 0;
         u128 leaf = 0;
         bool o = false;
+        const volatile int32_t *vk = keys, *vv = vals;
         for (int s = tid; s < slots; s += gs) {
-            if (keys[s] >= 0 && vals[s] >= a.kq) {
+            const int32_t key = vk[s], cnt = vv[s];
+            if (key >= 0 && cnt >= a.kq) {
                 ++c;
-                if (a.k == 2) add_u128(leaf, binom_lookup(a.binom, a.kq, vals[s], o), o);
+                if (a.k == 2) add_u128(leaf, binom_lookup(a.binom, a.kq, cnt, o), o);
             }
         }
         // group reductions through the warp sums and (for CTAs) shared memory
@@ -265,12 +267,16 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
     }
     // ---- pass B
     const int32_t c = a.cand_count[u];
-    if (tid == 0) shared_int[0] = 0;
+    if (tid == 0) { shared_int[0] = 0; shared_int[1] = 0; }
     G::sync();
-    for (int s = tid; s < slots; s += gs) {
-        if (keys[s] >= 0 && vals[s] >= a.kq) {
-            int idx = atomicAdd(&shared_int[0], 1);
-            sortbuf[idx] = rank_key(g.degA, keys[s]);
+    {
+        const volatile int32_t *vk = keys, *vv = vals;
+        for (int s = tid; s < slots; s += gs) {
+            const int32_t key = vk[s], cnt = vv[s];
+            if (key >= 0 && cnt >= a.kq) {
+                int idx = atomicAdd(&shared_int[0], 1);
+                sortbuf[idx] = rank_key(g.degA, key);
+            }
         }
     }
     G::sync();
@@ -288,11 +294,46 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
         if (slot >= 0) vals[slot] = -1 - i;
     }
     G::sync();
+    // Position order (the bitmap analogue of Sec. V-B's reordering, per root):
+    // the positions of N(u) sorted by how many candidates contain them, most
+    // shared first, so the common neighbourhoods deep in the tree gather in the
+    // first words of C_R.  Positions no candidate contains get no bit at all.
+    int32_t *pc = a.poscnt + g.offA[u];
+    int32_t *pm = a.posmap + g.offA[u];
+    const volatile int32_t *vvals = vals;
+    for_each_wedge<NW>(g, u, [&](int32_t w, int32_t i) {
+        const int32_t slot = table_find(keys, log2slots, w, a.status);
+        if (slot >= 0 && vvals[slot] < 0) atomicAdd(&pc[i], 1);
+    });
+    G::sync();
+    for (int i = tid; i < d; i += gs) {
+        const int32_t cnt = __ldcg(&pc[i]);
+        if (cnt > 0) {
+            const int t = atomicAdd(&shared_int[1], 1);
+            sortbuf[t] = ((uint64_t)(0xffffffffu - (uint32_t)cnt) << 32) | (uint32_t)i;
+        }
+    }
+    G::sync();
+    const int dn = ((volatile int32_t *)shared_int)[1];
+    P = 1;
+    while (P < dn) P <<= 1;
+    for (int i = dn + tid; i < P; i += gs) sortbuf[i] = ~0ull;
+    G::sync();
+    group_bitonic_u64(sortbuf, P, tid, gs, NW > 1);
+    for (int t = tid; t < dn; t += gs) pm[(uint32_t)sortbuf[t]] = t;
+    G::sync();
+    // R block of the root, word-major in pairs: words 2*pw and 2*pw+1 of row x
+    // sit at pair pw * c + x, so the first pair of every row forms one
+    // contiguous c * 8 B block (deep C_R spans rarely go past it).
     uint32_t *Rb = a.R + a.r_off[u];
     for_each_wedge<NW>(g, u, [&](int32_t w, int32_t i) {
         const int32_t slot = table_find(keys, log2slots, w, a.status);
-        const int32_t v = slot >= 0 ? vals[slot] : 0;
-        if (v < 0) atomicOr(&Rb[(int64_t)(-1 - v) * WR + (i >> 5)], 1u << (i & 31));
+        const int32_t v = slot >= 0 ? vvals[slot] : 0;
+        if (v < 0) {
+            const int32_t np = __ldcg(&pm[i]);
+            const int64_t x = -1 - v;
+            atomicOr(&Rb[2 * ((int64_t)(np >> 6) * c + x) + ((np >> 5) & 1)], 1u << (np & 31));
+        }
     });
     G::sync();
 }
@@ -418,7 +459,7 @@ __device__ __forceinline__ void root_sizes(const CountArgs &a, int64_t r, int64_
     const int32_t cc = a.cand_count[r];
     if (cc < a.k - 1 || cc == 0) return;
     c = cc;
-    wr = (int64_t)cc * ((a.g.degA[r] + 31) >> 5);
+    wr = (int64_t)cc * row_stride(a.g.degA[r]);
     wl = a.k >= 4 ? (int64_t)cc * ((cc + 31) >> 5) : 0;
 }
 
@@ -518,10 +559,38 @@ cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *
 }
 
 // ---------------------------------------------------------------------------
+// Root blocks (written in pass B and by k_pairs), for a root with d neighbours
+// and c candidates, np = row_stride(d) / 2 word pairs per R row, WL = ceil(c/32):
+//   R: pair pw of candidate x at ((uint2*)Rb)[pw * c + x]   (word-major)
+//   S: word w of candidate y at Sb[w * c + y]               (word-major)
+// Lanes holding neighbouring candidates therefore read neighbouring addresses.
+
+__device__ __forceinline__ int popc2(uint2 a, uint2 b) { return __popc(a.x & b.x) + __popc(a.y & b.y); }
+__device__ __forceinline__ uint2 and2(uint2 a, uint2 b) { return make_uint2(a.x & b.x, a.y & b.y); }
+
+// Pairs of row x holding all of its set bits (its span).  Warp-wide.
+__device__ __forceinline__ int row_span_pairs(const uint2 *Rp, int64_t c, int64_t x, int npairs) {
+    const int lane = threadIdx.x & 31;
+    int span = 0;
+    for (int base = 0; base < npairs; base += 32) {
+        const int pw = base + lane;
+        bool nz = false;
+        if (pw < npairs) {
+            const uint2 v = Rp[pw * c + x];
+            nz = (v.x | v.y) != 0u;
+        }
+        const unsigned m = __ballot_sync(kFull, nz);
+        if (m) span = base + 32 - __clz(m);
+    }
+    return span;
+}
+
+// ---------------------------------------------------------------------------
 // Level-2 rows.  Warp per candidate j of a root: for every later candidate x,
-// n = popc(R_j & R_x).  k == 3: (u, j, x) is a leaf and adds C(n, kq) when
-// n >= kq.  k >= 4: the ballot of (n >= kq) over 32 consecutive x is word
-// x/32 of S_j; units with |S_j| >= k-2 go to the enumeration list.
+// n = popc(R_j & R_x) over the span of R_j.  k == 3: (u, j, x) is a leaf and
+// adds C(n, kq) when n >= kq.  k >= 4: the ballot of (n >= kq) over 32
+// consecutive x is word x/32 of S_j; units with |S_j| >= k-2 go to the
+// enumeration list.
 template <bool STATS>
 __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
     const int lane = threadIdx.x & 31;
@@ -534,11 +603,16 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
         if (gidx >= a.n_cand || past_deadline(a)) break;
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
-        const int32_t c = a.cand_count[r];
-        const int32_t WR = (a.g.degA[r] + 31) >> 5;
-        const int32_t WL = (c + 31) >> 5;
-        const uint32_t *Rb = a.R + a.r_off[r];
-        const uint32_t *Rj = Rb + (int64_t)j * WR;
+        const int64_t c = a.cand_count[r];
+        const int32_t d = a.g.degA[r];
+        const int32_t WRm = (d + 31) >> 5;  // words of the full-width model (statistics)
+        const int npairs = row_stride(d) >> 1;
+        const int32_t WL = (int32_t)((c + 31) >> 5);
+        const uint2 *Rp = reinterpret_cast<const uint2 *>(a.R + a.r_off[r]);
+        const int s2 = row_span_pairs(Rp, c, j, npairs);
+        uint2 rj0 = make_uint2(0, 0), rj1 = make_uint2(0, 0);
+        if (s2 > 0) rj0 = Rp[j];
+        if (s2 > 1) rj1 = Rp[c + j];
         u128 row_acc = 0;
         int passes = 0;
         for (int32_t t = (j + 1) >> 5; t < WL; ++t) {
@@ -546,8 +620,12 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
             const bool valid = x > j && x < c;
             int n = 0;
             if (valid) {
-                const uint32_t *Rx = Rb + (int64_t)x * WR;
-                for (int32_t w = 0; w < WR; ++w) n += __popc(Rj[w] & Rx[w]);
+                if (s2 <= 2) {
+                    n = popc2(rj0, Rp[x]);
+                    if (s2 > 1) n += popc2(rj1, Rp[c + x]);
+                } else {
+                    for (int pw = 0; pw < s2; ++pw) n += popc2(Rp[pw * c + j], Rp[pw * c + x]);
+                }
             }
             const bool pass = valid && n >= a.kq;
             const unsigned m = __ballot_sync(kFull, pass);
@@ -555,7 +633,7 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
             if (a.k == 3) {
                 if (pass) add_u128(row_acc, binom_lookup(a.binom, a.kq, n, ovf), ovf);
             } else if (lane == 0) {
-                a.S[a.s_off[r] + (int64_t)j * WL + t] = m;
+                a.S[a.s_off[r] + (int64_t)t * c + j] = m;
             }
         }
         if (a.k >= 4 && lane == 0 && passes >= a.k - 2) {
@@ -571,12 +649,12 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
         if (STATS && lane == 0) {
             atomicAdd(&a.stats->evals[2], 1ull);
             atomicAdd(&a.stats->passed[2], 1ull);
-            atomicAdd(&a.stats->words_r, (unsigned long long)WR);
+            atomicAdd(&a.stats->words_r, (unsigned long long)WRm);
             atomicAdd(&a.stats->words_l, (unsigned long long)WL);
             if (a.k == 3) {
                 atomicAdd(&a.stats->evals[3], (unsigned long long)passes);
                 atomicAdd(&a.stats->passed[3], (unsigned long long)passes);
-                atomicAdd(&a.stats->words_r, (unsigned long long)passes * WR);
+                atomicAdd(&a.stats->words_r, (unsigned long long)passes * WRm);
             } else if (passes >= a.k - 2) {
                 atomicAdd(&a.stats->units, 1ull);
             }
@@ -608,21 +686,41 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
 // C_L) and evaluates them side by side, one child per lane, against the
 // parent's C_R and C_L, which sit in shared memory and are read by every lane
 // at once (the siblings-share-the-parent idea of Sec. IV's hybrid search).
-// Children at the last level are leaves and add C(|C_R'|, kq); the others that
-// pass both pruning tests (|C_R'| >= kq, |C_L'| >= k - |L'|) are entered one by
-// one, their C_R' and C_L' rebuilt cooperatively (lanes over words).
 //
-// Per warp, for each level lv = |L| - 2 in [0, k-2):
-//   CR[lv] : WRmax words, CL[lv] : WLmax words, xs[lv] : 32 child ids,
-//   cursor[lv] (next C_L position to take), dmask[lv] (children still to enter).
+// At a node two levels above the leaves (|L| = k - 2) each lane finishes its
+// child y on its own: C_R(y) = C_R & R_y stays in registers and the lane walks
+// the leaves x in C_L & S_y after y, adding C(|C_R(y) & R_x|, kq) for each
+// that reaches kq (Alg. 1's last two levels, one subtree per lane).
+// Internal children that pass both pruning tests (|C_R'| >= kq, |C_L'| >=
+// k - |L'|) are entered one by one, their C_R' and C_L' rebuilt cooperatively.
+//
+// C_R is read only up to its span (word pairs holding its set bits); thanks to
+// the per-root position order, spans are one pair deep in most of the tree.
+//
+// Per warp, for each level lv = |L| - 2 in [0, k-3):
+//   CR[lv] : wr words, CL[lv] : wl words, xs[lv] : 32 child ids;
+//   cursor[lv] (next C_L position to take), dmask[lv] (children still to
+//   enter), span[lv] (pair span of CR[lv]).
 struct EnumLayout {
-    int wr, wl;     // row capacities in words
-    int levels;     // k - 2
+    int wr, wl;     // row capacities in words (both even)
+    int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
     __host__ __device__ int level_words() const { return wr + wl + 32; }
-    __host__ __device__ int warp_words() const { return levels * level_words() + 2 * kMaxPQ; }
+    __host__ __device__ int warp_words() const { return levels * level_words() + 3 * kMaxPQ + 2; }
 };
 
-// The next <= 32 set bits of CL at or after *cursor, in order, into xs.
+// Position of the n-th (from 0) set bit of w (n < popc(w)).
+__device__ __forceinline__ int select_bit(uint32_t w, int n) {
+    int pos = 0, c;
+    c = __popc(w & 0xffffu); if (n >= c) { n -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);   if (n >= c) { n -= c; w >>= 8;  pos += 8; }
+    c = __popc(w & 0xfu);    if (n >= c) { n -= c; w >>= 4;  pos += 4; }
+    c = __popc(w & 0x3u);    if (n >= c) { n -= c; w >>= 2;  pos += 2; }
+    if (n >= (int)(w & 1u)) pos += 1;
+    return pos;
+}
+
+// The next <= 32 set bits of CL at or after cursor, in order, into xs: lane t
+// finds the t-th bit of the round by a shuffle search over the word counts.
 __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c, int &cursor, int32_t *xs) {
     const int lane = threadIdx.x & 31;
     int got = 0;
@@ -634,24 +732,24 @@ __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c
         if (lane == 0) word &= ~0u << (pos & 31);
         const int cnt = __popc(word);
         const int incl = warp_incl_scan(cnt);
-        const int excl = incl - cnt;
         const int total = __shfl_sync(kFull, incl, 31);
-        const int need = 32 - got;
-        const int take = min(cnt, max(0, need - excl));
-        uint32_t wv = word;
-        int last = 0;
-        for (int b = 0; b < take; ++b) {
-            const int bit = __ffs(wv) - 1;
-            wv &= wv - 1;
-            xs[got + excl + b] = (wi << 5) + bit;
-            last = (wi << 5) + bit;
+        const int room = 32 - got;
+        int src = 0;
+#pragma unroll
+        for (int b = 16; b >= 1; b >>= 1) {
+            const int v = __shfl_sync(kFull, incl, src + b - 1);
+            if (v <= lane) src += b;
         }
-        if (total <= need) {
+        src = min(src, 31);
+        const uint32_t ws = __shfl_sync(kFull, word, src);
+        const int ex = __shfl_sync(kFull, incl - cnt, src);
+        const int x = ((w0 + src) << 5) + select_bit(ws, lane - ex);
+        if (lane < min(total, room)) xs[got + lane] = x;
+        if (total <= room) {
             got += total;
             pos = (w0 + 32) << 5;
         } else {
-            const int holder = __ffs(__ballot_sync(kFull, incl >= need)) - 1;
-            pos = __shfl_sync(kFull, last, holder) + 1;
+            pos = __shfl_sync(kFull, x, room - 1) + 1;
             got = 32;
         }
     }
@@ -660,24 +758,32 @@ __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c
     return got;
 }
 
+constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never above 2^128)
+
 template <bool STATS>
 __global__ void __launch_bounds__(256)
 k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     extern __shared__ __align__(16) uint32_t smem_stack[];
+    __shared__ ulonglong2 s_binom[kSmemBinom];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int k = a.k, kq = a.kq;
+    for (int n = threadIdx.x; n < kSmemBinom; n += blockDim.x)
+        s_binom[n] = n <= a.binom.nmax ? a.binom.c[(size_t)kq * (a.binom.nmax + 1) + n] : make_ulonglong2(0, 0);
+    __syncthreads();
     uint32_t *base = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
                             : smem_stack + (int64_t)wib * lay.warp_words();
     int32_t *cursor = reinterpret_cast<int32_t *>(base + lay.levels * lay.level_words());
     uint32_t *dmask = reinterpret_cast<uint32_t *>(cursor + kMaxPQ);
-    auto CR = [&](int lv) { return base + (int64_t)lv * lay.level_words(); };
+    int32_t *spanp = reinterpret_cast<int32_t *>(dmask + kMaxPQ);
+    auto CR = [&](int lv) { return reinterpret_cast<uint2 *>(base + (int64_t)lv * lay.level_words()); };
     auto CL = [&](int lv) { return base + (int64_t)lv * lay.level_words() + lay.wr; };
     auto XS = [&](int lv) { return reinterpret_cast<int32_t *>(base + (int64_t)lv * lay.level_words() + lay.wr + lay.wl); };
 
-    const int k = a.k, kq = a.kq;
     u128 acc = 0;
     bool ovf = false;
-    unsigned long long words = 0;  // C_R + C_L words of the evaluated children (algorithmic work)
+    unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
+    unsigned long long st_evals[2] = {0, 0}, st_passed[2] = {0, 0}, st_wr = 0, st_wl = 0;
     const int n_units = *a.n_units;
     while (true) {
         int uidx = 0;
@@ -687,16 +793,22 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
         const int64_t gidx = a.units[uidx];
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
-        const int32_t c = a.cand_count[r];
-        const int32_t WR = (a.g.degA[r] + 31) >> 5;
-        const int32_t WL = (c + 31) >> 5;
-        const uint32_t *Rb = a.R + a.r_off[r];
-        const uint32_t *Sb = a.S + a.s_off[r];
+        const int64_t c = a.cand_count[r];
+        const int32_t d = a.g.degA[r];
+        const int32_t WRm = (d + 31) >> 5;
+        const int npairs = row_stride(d) >> 1;
+        const int32_t WL = (int32_t)((c + 31) >> 5);
+        const uint2 *Rp = reinterpret_cast<const uint2 *>(a.R + a.r_off[r]);
+        const uint32_t *St = a.S + a.s_off[r];
         u128 unit_acc = 0;
-        // level 2 node {u, j}: C_R = R_j, C_L = S_j
-        for (int w = lane; w < WR; w += 32) CR(0)[w] = Rb[(int64_t)j * WR + w];
-        for (int w = lane; w < WL; w += 32) CL(0)[w] = Sb[(int64_t)j * WL + w];
-        if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; }
+        // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
+        {
+            for (int pw = lane; pw < npairs; pw += 32) CR(0)[pw] = Rp[pw * c + j];
+            const int lo = (j + 1) >> 5;
+            for (int w = lo + lane; w < WL; w += 32) CL(0)[w] = St[(int64_t)w * c + j];
+            const int sp = row_span_pairs(Rp, c, j, npairs);
+            if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; spanp[0] = sp; }
+        }
         __syncwarp();
         int lv = 0;
         unsigned batches = 0;
@@ -706,21 +818,33 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
             if (dm != 0) {
                 const int t = __ffs(dm) - 1;
                 const int32_t x = XS(lv)[t];
+                const int sp = spanp[lv];
                 __syncwarp();
                 if (lane == 0) dmask[lv] = dm & (dm - 1);
-                const uint32_t *cr = CR(lv), *cl = CL(lv);
-                uint32_t *cr2 = CR(lv + 1), *cl2 = CL(lv + 1);
-                const uint32_t *Rx = Rb + (int64_t)x * WR, *Sx = Sb + (int64_t)x * WL;
-                const int w0 = (x + 1) >> 5;
-                for (int w = lane; w < WR; w += 32) cr2[w] = cr[w] & Rx[w];
-                for (int w = lane; w < WL; w += 32) cl2[w] = w >= w0 ? (cl[w] & Sx[w]) : 0u;
-                if (lane == 0) { cursor[lv + 1] = x + 1; dmask[lv + 1] = 0; }
+                const uint2 *cr = CR(lv);
+                uint2 *cr2 = CR(lv + 1);
+                const uint32_t *cl = CL(lv);
+                uint32_t *cl2 = CL(lv + 1);
+                int nsp = 0;
+                for (int b = 0; b < sp; b += 32) {
+                    const int pw = b + lane;
+                    uint2 v = make_uint2(0, 0);
+                    if (pw < sp) {
+                        v = and2(cr[pw], Rp[pw * c + x]);
+                        cr2[pw] = v;
+                    }
+                    const unsigned m = __ballot_sync(kFull, (v.x | v.y) != 0u);
+                    if (m) nsp = b + 32 - __clz(m);
+                }
+                const int lo = (x + 1) >> 5;
+                for (int w = lo + lane; w < WL; w += 32) cl2[w] = cl[w] & St[(int64_t)w * c + x];
+                if (lane == 0) { cursor[lv + 1] = x + 1; dmask[lv + 1] = 0; spanp[lv + 1] = nsp; }
                 __syncwarp();
                 ++lv;
                 continue;
             }
             int cur = cursor[lv];
-            const int got = gather_children(CL(lv), WL, c, cur, XS(lv));
+            const int got = gather_children(CL(lv), WL, (int)c, cur, XS(lv));
             if (lane == 0) cursor[lv] = cur;
             if (got == 0) {
                 __syncwarp();
@@ -728,37 +852,79 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
                 --lv;
                 continue;
             }
-            const int ell = lv + 2;          // |L| of the node
-            const bool leaf = (ell + 1 == k);
-            const uint32_t *cr = CR(lv), *cl = CL(lv);
+            const int ell = lv + 2;  // |L| of the node
+            const int sp = spanp[lv];
+            const uint2 *cr = CR(lv);
+            const uint32_t *cl = CL(lv);
+            if (ell + 2 == k) {
+                // children y are leaf parents: one per lane, leaves walked in the lane
+                if (lane < got) {
+                    const int32_t y = XS(lv)[lane];
+                    uint2 c0 = make_uint2(0, 0), c1 = make_uint2(0, 0);
+                    int ny = 0;
+                    if (sp <= 2) {
+                        if (sp > 0) { c0 = and2(cr[0], Rp[y]); ny += __popc(c0.x) + __popc(c0.y); }
+                        if (sp > 1) { c1 = and2(cr[1], Rp[c + y]); ny += __popc(c1.x) + __popc(c1.y); }
+                    } else {
+                        for (int pw = 0; pw < sp; ++pw) ny += popc2(cr[pw], Rp[pw * c + y]);
+                    }
+                    words += 2 * sp;
+                    if (STATS) { st_evals[0] += 1; st_wr += WRm; }
+                    if (ny >= kq) {
+                        if (STATS) { st_passed[0] += 1; st_wl += WL; }
+                        for (int w = (y + 1) >> 5; w < WL; ++w) {
+                            uint32_t bits = cl[w] & St[(int64_t)w * c + y];
+                            words += 1;
+                            while (bits) {
+                                const int32_t x = (w << 5) + __ffs(bits) - 1;
+                                bits &= bits - 1;
+                                int n;
+                                if (sp <= 2) {
+                                    n = popc2(c0, Rp[x]);
+                                    if (sp > 1) n += popc2(c1, Rp[c + x]);
+                                } else {
+                                    n = 0;
+                                    for (int pw = 0; pw < sp; ++pw) n += popc2(and2(cr[pw], Rp[pw * c + y]), Rp[pw * c + x]);
+                                }
+                                words += 2 * sp;
+                                if (STATS) { st_evals[1] += 1; st_wr += WRm; }
+                                if (n >= kq) {
+                                    if (STATS) st_passed[1] += 1;
+                                    if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                    else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                continue;  // no child to enter: the next batch of this node
+            }
+            // internal children: evaluate both pruning tests, flag those to enter
             int n = 0;
             int32_t x = 0;
             if (lane < got) {
                 x = XS(lv)[lane];
-                const uint32_t *Rx = Rb + (int64_t)x * WR;
-                for (int w = 0; w < WR; ++w) n += __popc(cr[w] & Rx[w]);
+                for (int pw = 0; pw < sp; ++pw) n += popc2(cr[pw], Rp[pw * c + x]);
+                words += 2 * sp;
             }
             const bool pass = lane < got && n >= kq;
             bool desc = false;
-            if (leaf) {
-                if (pass) add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
-            } else if (pass) {
-                const uint32_t *Sx = Sb + (int64_t)x * WL;
+            if (pass) {
+                const int lo = (x + 1) >> 5;
                 int m = 0;
-                for (int w = (x + 1) >> 5; w < WL; ++w) m += __popc(cl[w] & Sx[w]);
+                for (int w = lo; w < WL; ++w) m += __popc(cl[w] & St[(int64_t)w * c + x]);
+                words += WL - lo;
                 desc = m >= k - (ell + 1);
             }
             const unsigned dmb = __ballot_sync(kFull, desc);
-            words += (unsigned long long)got * WR;
-            if (!leaf) words += (unsigned long long)__popc(__ballot_sync(kFull, pass)) * WL;
             if (STATS) {
                 const unsigned pm = __ballot_sync(kFull, pass);
                 if (lane == 0) {
                     atomicAdd(&a.stats->evals[ell + 1], (unsigned long long)got);
                     atomicAdd(&a.stats->passed[ell + 1], (unsigned long long)__popc(pm));
-                    atomicAdd(&a.stats->words_r, (unsigned long long)got * WR);
-                    if (!leaf) atomicAdd(&a.stats->words_l, (unsigned long long)__popc(pm) * WL);
-
+                    atomicAdd(&a.stats->words_r, (unsigned long long)got * WRm);
+                    atomicAdd(&a.stats->words_l, (unsigned long long)__popc(pm) * WL);
                 }
             }
             __syncwarp();
@@ -772,22 +938,33 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
         add_u128(acc, unit_acc, ovf);
     }
     acc = warp_sum_u128(acc, ovf);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
     if (lane == 0) {
         if (ovf) atomicOr(a.status, kStOverflow);
         atomic_add_u128(a.acc, acc, a.status);
         atomicAdd(a.enum_words, words);
     }
+    if (STATS) {
+        // the last two levels were counted per lane
+        atomicAdd(&a.stats->evals[k - 1], st_evals[0]);
+        atomicAdd(&a.stats->evals[k], st_evals[1]);
+        atomicAdd(&a.stats->passed[k - 1], st_passed[0]);
+        atomicAdd(&a.stats->passed[k], st_passed[1]);
+        atomicAdd(&a.stats->words_r, st_wr);
+        atomicAdd(&a.stats->words_l, st_wl);
+    }
 }
 
 cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, int max_wl, int n_sms,
                              cudaStream_t st) {
-    EnumLayout lay{max_wr, max_wl, a.k - 2};
+    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, a.k - 3)};
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;
     const size_t smem = per_warp * warps_per_cta;
     const bool use_smem = smem <= 160 * 1024;
     int grid = n_sms * 4;
-    if (n_warps_hint > 0) grid = max(1, n_warps_hint / warps_per_cta);
+    if (n_warps_hint > 0) grid = std::max(1, n_warps_hint / warps_per_cta);
     uint32_t *gstack = nullptr;
     cudaError_t err;
     if (use_smem) {
@@ -796,7 +973,7 @@ cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, i
         if (err != cudaSuccess) return err;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_cta, smem);
-        if (n_warps_hint <= 0) grid = n_sms * max(1, per_sm);
+        if (n_warps_hint <= 0) grid = n_sms * std::max(1, per_sm);
         kern<<<grid, 32 * warps_per_cta, smem, st>>>(a, lay, nullptr);
         ++t_launches;
     } else {
