@@ -701,11 +701,17 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
 //   CR[lv] : wr words, CL[lv] : wl words, xs[lv] : 32 child ids;
 //   cursor[lv] (next C_L position to take), dmask[lv] (children still to
 //   enter), span[lv] (pair span of CR[lv]).
+constexpr int kLeafList = 256;  // nonzero leaf words staged per warp before they are expanded
+
 struct EnumLayout {
     int wr, wl;     // row capacities in words (both even)
     int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
+    // per warp: CRY (32 x uint4) | leaf masks | leaf tags | levels x (CR | CL | xs) | scalars
+    __host__ __device__ int staging_words() const { return 32 * 4 + 2 * kLeafList; }
     __host__ __device__ int level_words() const { return wr + wl + 32; }
-    __host__ __device__ int warp_words() const { return levels * level_words() + 3 * kMaxPQ + 2; }
+    __host__ __device__ int warp_words() const {
+        return (staging_words() + levels * level_words() + 3 * kMaxPQ + 2 + 3) & ~3;
+    }
 };
 
 // Position of the n-th (from 0) set bit of w (n < popc(w)).
@@ -771,8 +777,12 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     for (int n = threadIdx.x; n < kSmemBinom; n += blockDim.x)
         s_binom[n] = n <= a.binom.nmax ? a.binom.c[(size_t)kq * (a.binom.nmax + 1) + n] : make_ulonglong2(0, 0);
     __syncthreads();
-    uint32_t *base = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
-                            : smem_stack + (int64_t)wib * lay.warp_words();
+    uint32_t *wbase = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
+                             : smem_stack + (int64_t)wib * lay.warp_words();
+    uint4 *CRY = reinterpret_cast<uint4 *>(wbase);              // C_R of each lane's leaf parent
+    uint32_t *LM = wbase + 32 * 4;                              // staged nonzero leaf words
+    uint32_t *LT = LM + kLeafList;                              // their tags: lane << 16 | word
+    uint32_t *base = wbase + lay.staging_words();
     int32_t *cursor = reinterpret_cast<int32_t *>(base + lay.levels * lay.level_words());
     uint32_t *dmask = reinterpret_cast<uint32_t *>(cursor + kMaxPQ);
     int32_t *spanp = reinterpret_cast<int32_t *>(dmask + kMaxPQ);
@@ -857,42 +867,108 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
             const uint2 *cr = CR(lv);
             const uint32_t *cl = CL(lv);
             if (ell + 2 == k) {
-                // children y are leaf parents: one per lane, leaves walked in the lane
+                // Children y are leaf parents.  Phase A: each lane forms C_R(y) =
+                // C_R & R_y (kept in CRY) and stages the nonzero words of its
+                // leaf set C_L & S_y (after y) in the warp's list.  Phase B: the
+                // staged leaves are dealt out 32 at a time, whatever parent they
+                // belong to, so every lane evaluates a leaf on every step.
+                int32_t y = 0;
+                bool py = false;
                 if (lane < got) {
-                    const int32_t y = XS(lv)[lane];
-                    uint2 c0 = make_uint2(0, 0), c1 = make_uint2(0, 0);
+                    y = XS(lv)[lane];
                     int ny = 0;
+                    uint4 cy = make_uint4(0, 0, 0, 0);
                     if (sp <= 2) {
-                        if (sp > 0) { c0 = and2(cr[0], Rp[y]); ny += __popc(c0.x) + __popc(c0.y); }
-                        if (sp > 1) { c1 = and2(cr[1], Rp[c + y]); ny += __popc(c1.x) + __popc(c1.y); }
+                        if (sp > 0) { const uint2 v = and2(cr[0], Rp[y]); cy.x = v.x; cy.y = v.y; }
+                        if (sp > 1) { const uint2 v = and2(cr[1], Rp[c + y]); cy.z = v.x; cy.w = v.y; }
+                        ny = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
                     } else {
                         for (int pw = 0; pw < sp; ++pw) ny += popc2(cr[pw], Rp[pw * c + y]);
                     }
+                    CRY[lane] = cy;
+                    py = ny >= kq;
                     words += 2 * sp;
-                    if (STATS) { st_evals[0] += 1; st_wr += WRm; }
-                    if (ny >= kq) {
-                        if (STATS) { st_passed[0] += 1; st_wl += WL; }
-                        for (int w = (y + 1) >> 5; w < WL; ++w) {
-                            uint32_t bits = cl[w] & St[(int64_t)w * c + y];
-                            words += 1;
-                            while (bits) {
-                                const int32_t x = (w << 5) + __ffs(bits) - 1;
-                                bits &= bits - 1;
-                                int n;
-                                if (sp <= 2) {
-                                    n = popc2(c0, Rp[x]);
-                                    if (sp > 1) n += popc2(c1, Rp[c + x]);
-                                } else {
-                                    n = 0;
-                                    for (int pw = 0; pw < sp; ++pw) n += popc2(and2(cr[pw], Rp[pw * c + y]), Rp[pw * c + x]);
+                }
+                if (STATS) {
+                    const unsigned pm = __ballot_sync(kFull, py);
+                    if (lane == 0) {
+                        st_evals[0] += got;
+                        st_passed[0] += __popc(pm);
+                        st_wr += (unsigned long long)got * WRm;
+                        st_wl += (unsigned long long)__popc(pm) * WL;
+                    }
+                }
+                const int lo_y = (y + 1) >> 5;
+                const int lo_min = (__shfl_sync(kFull, y, 0) + 1) >> 5;  // lane 0 holds the smallest y
+                if (sp <= 2) {
+                    int nl = 0;
+                    for (int w = lo_min; w < WL; ++w) {
+                        uint32_t mk = 0;
+                        if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; words += 1; }
+                        const unsigned nz = __ballot_sync(kFull, mk != 0u);
+                        if (mk) {
+                            const int at = nl + __popc(nz & ((1u << lane) - 1u));
+                            LM[at] = mk;
+                            LT[at] = ((uint32_t)lane << 16) | (uint32_t)w;
+                        }
+                        nl += __popc(nz);
+                        if (nl > kLeafList - 32 || (w + 1 == WL && nl > 0)) {
+                            __syncwarp();
+                            // Phase B over LM[0, nl)
+                            for (int e0 = 0; e0 < nl; e0 += 32) {
+                                const int e = e0 + lane;
+                                const uint32_t m = e < nl ? LM[e] : 0u;
+                                const uint32_t tg = e < nl ? LT[e] : 0u;
+                                const int cnt = __popc(m);
+                                const int incl = warp_incl_scan(cnt);
+                                const int total = __shfl_sync(kFull, incl, 31);
+                                for (int rb = 0; rb < total; rb += 32) {
+                                    const int rk = rb + lane;
+                                    int src = 0;
+#pragma unroll
+                                    for (int b = 16; b >= 1; b >>= 1) {
+                                        const int v = __shfl_sync(kFull, incl, src + b - 1);
+                                        if (v <= rk) src += b;
+                                    }
+                                    src = min(src, 31);
+                                    const uint32_t ws = __shfl_sync(kFull, m, src);
+                                    const int ex = __shfl_sync(kFull, incl - cnt, src);
+                                    const uint32_t t = __shfl_sync(kFull, tg, src);
+                                    if (rk < total) {
+                                        const int32_t x = (int32_t)((t & 0xffffu) << 5) + select_bit(ws, rk - ex);
+                                        const uint4 cy = CRY[t >> 16];
+                                        int n = popc2(make_uint2(cy.x, cy.y), Rp[x]);
+                                        if (sp > 1) n += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
+                                        words += 2 * sp;
+                                        if (STATS) { st_evals[1] += 1; st_wr += WRm; }
+                                        if (n >= kq) {
+                                            if (STATS) st_passed[1] += 1;
+                                            if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                            else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
+                                        }
+                                    }
                                 }
-                                words += 2 * sp;
-                                if (STATS) { st_evals[1] += 1; st_wr += WRm; }
-                                if (n >= kq) {
-                                    if (STATS) st_passed[1] += 1;
-                                    if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
-                                    else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
-                                }
+                            }
+                            nl = 0;
+                            __syncwarp();
+                        }
+                    }
+                } else if (py) {
+                    // wide C_R (rare): the lane walks its own leaves, C_R(y) & R_x re-read per leaf
+                    for (int w = lo_y; w < WL; ++w) {
+                        uint32_t bits = cl[w] & St[(int64_t)w * c + y];
+                        words += 1;
+                        while (bits) {
+                            const int32_t x = (w << 5) + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            int n = 0;
+                            for (int pw = 0; pw < sp; ++pw) n += popc2(and2(cr[pw], Rp[pw * c + y]), Rp[pw * c + x]);
+                            words += 2 * sp;
+                            if (STATS) { st_evals[1] += 1; st_wr += WRm; }
+                            if (n >= kq) {
+                                if (STATS) st_passed[1] += 1;
+                                if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
                             }
                         }
                     }
