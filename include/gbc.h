@@ -159,6 +159,40 @@ gbc_status gbc_count_ex(gbc_graph_t g, int p, int q, const gbc_count_options *op
 gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor,
                               gbc_u128 *per_root, gbc_u128 *total);
 
+/* Most higher-ranked 2-hop neighbours a vertex of U may have in
+ * gbc_count_p2_noalloc (its fixed scratch holds one hash table per CTA). */
+#define GBC_NOALLOC_MAX_2HOP 4096
+
+/*
+ * gbc_count_p2_noalloc -- the number of (2,q)-bicliques (|L| = 2 on U, |R| = q
+ * on V) for callers that cannot allocate device memory.  The paper has no
+ * counterpart of this entry point.
+ *
+ * Some callers cannot call cudaMalloc: code living inside another framework's
+ * memory pool, plug-ins allowed to touch only the buffers handed to them, or
+ * processes whose allocator is reserved.  They pass the graph's CSR arrays in
+ * device memory and get the count back; the call itself allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  Its only scratch is one
+ * static device array of this library, 16 MiB + 256 B, which every GPU that
+ * loads the library holds until the process exits.
+ *   nU, nV, offU_d, adjU_d, offV_d, adjV_d: device CSR arrays on the current
+ *     device, with the layout rules of gbc_load_graph (not validated here);
+ *   q: 1..GBC_MAX_PQ;  stream: a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream);  out: host, written on GBC_OK.
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array and it keeps the last
+ * call's contents (the call clears what must start at zero), so calls that
+ * overlap on the GPU -- from other streams or threads -- race and give wrong
+ * results: serialise them.
+ * Errors: GBC_ERR_ARG; GBC_ERR_OOM when a vertex of U has more than
+ * GBC_NOALLOC_MAX_2HOP higher-ranked (by (degree, id)) 2-hop neighbours, the
+ * size its fixed scratch holds; GBC_ERR_OVERFLOW; GBC_ERR_CUDA.
+ */
+gbc_status gbc_count_p2_noalloc(int32_t nU, int32_t nV, const int32_t *offU_d, const int32_t *adjU_d,
+                                const int32_t *offV_d, const int32_t *adjV_d, int q, void *stream,
+                                gbc_u128 *out);
+
 /* Human-readable text of a status, and the calling thread's last error. */
 const char *gbc_status_string(gbc_status s);
 const char *gbc_last_error(void);

@@ -111,6 +111,8 @@ SIGNATURES = {
                                     ctypes.POINTER(U128), ctypes.POINTER(CountInfo)]),
     "gbc_count_per_root": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(U128), ctypes.POINTER(U128)]),
+    "gbc_count_p2_noalloc": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
+                                            ctypes.POINTER(U128)]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbc_last_error": (ctypes.c_char_p, []),
 }
@@ -252,3 +254,18 @@ class Context:
     def load(self, g) -> Graph:
         """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""
         return self.load_graph(g.n_u, g.n_v, g.off_u, g.adj_u, g.off_v, g.adj_v)
+
+
+def count_p2_noalloc(n_u: int, n_v: int, off_u, adj_u, off_v, adj_v, q: int, stream=None) -> int:
+    """(2,q)-biclique count from CUDA tensors through the entry point that
+    allocates nothing (its scratch is a fixed static device array).  The four
+    arrays must be int32 CUDA tensors on the current device."""
+    arrays = (off_u, adj_u, off_v, adj_v)
+    if not all(_is_cuda_tensor(x) for x in arrays):
+        raise TypeError("count_p2_noalloc takes int32 CUDA tensors")
+    handle = getattr(stream, "cuda_stream", stream)
+    out = U128()
+    _check(load_library().gbc_count_p2_noalloc(n_u, n_v, *[ctypes.c_void_p(x.data_ptr()) for x in arrays], q,
+                                               ctypes.c_void_p(handle or 0), ctypes.byref(out)),
+           "gbc_count_p2_noalloc")
+    return out.value()

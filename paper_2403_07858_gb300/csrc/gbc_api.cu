@@ -26,6 +26,8 @@ static gbc_status fail(gbc_status s, const char *fmt, ...) {
     return s;
 }
 
+void gbc::set_last_error(const char *msg) { snprintf(t_err, sizeof t_err, "%s", msg); }
+
 #define CK(expr)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (expr);                                                              \

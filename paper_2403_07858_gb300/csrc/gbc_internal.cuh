@@ -109,6 +109,34 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
+// (hi, lo) <- (hi, lo) * m / j, exact when j divides the 160-bit product (as it
+// does in C(n, j) = C(n, j-1) * (n - j + 1) / j); returns true when the
+// quotient does not fit in 128 bits.
+__device__ __forceinline__ bool mul_div_small(uint64_t &lo, uint64_t &hi, uint32_t m, uint32_t j) {
+    // (hi, lo) * m  ->  (r2, r1, r0)
+    uint64_t p0_lo = lo * (uint64_t)m, p0_hi = __umul64hi(lo, (uint64_t)m);
+    uint64_t p1_lo = hi * (uint64_t)m, p1_hi = __umul64hi(hi, (uint64_t)m);
+    uint64_t r0 = p0_lo;
+    uint64_t r1 = p0_hi + p1_lo;
+    uint64_t r2 = p1_hi + (r1 < p0_hi ? 1ull : 0ull);
+    // divide (r2, r1, r0) by j (<= 16), most significant limb first
+    uint64_t q2 = r2 / j, rem = r2 % j;
+    uint64_t limbs[2] = {r1, r0}, q[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        uint64_t a = (rem << 32) | (limbs[t] >> 32);
+        uint64_t qa = a / j;
+        rem = a % j;
+        uint64_t b = (rem << 32) | (limbs[t] & 0xffffffffull);
+        uint64_t qb = b / j;
+        rem = b % j;
+        q[t] = (qa << 32) | qb;
+    }
+    hi = q[0];
+    lo = q[1];
+    return q2 != 0;
+}
+
 // Per-count search statistics (filled only when stats are requested).
 struct SearchStats {
     unsigned long long roots;
@@ -119,6 +147,9 @@ struct SearchStats {
     unsigned long long words_r;
     unsigned long long words_l;
 };
+
+// Sets the text gbc_last_error() returns on the calling thread.
+void set_last_error(const char *msg);
 
 // Kernels launched by the calling thread since the last reset (a count runs on
 // the calling thread, serialised per context).

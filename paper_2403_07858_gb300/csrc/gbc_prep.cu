@@ -210,31 +210,6 @@ cudaError_t launch_mirror(const int32_t *offA, const int32_t *adjA, int32_t nA, 
 // C(n, j) = C(n, j-1) * (n - j + 1) / j, which is exact in integers: the
 // 160-bit product is divided by j with 64-bit limbs.  The first j whose value
 // leaves 128 bits marks this n, and every larger j, as overflowing.
-__device__ __forceinline__ bool mul_div_small(uint64_t &lo, uint64_t &hi, uint32_t m, uint32_t j) {
-    // (hi, lo) * m  ->  (r2, r1, r0)
-    uint64_t p0_lo = lo * (uint64_t)m, p0_hi = __umul64hi(lo, (uint64_t)m);
-    uint64_t p1_lo = hi * (uint64_t)m, p1_hi = __umul64hi(hi, (uint64_t)m);
-    uint64_t r0 = p0_lo;
-    uint64_t r1 = p0_hi + p1_lo;
-    uint64_t r2 = p1_hi + (r1 < p0_hi ? 1ull : 0ull);
-    // divide (r2, r1, r0) by j (<= 16), most significant limb first
-    uint64_t q2 = r2 / j, rem = r2 % j;
-    uint64_t limbs[2] = {r1, r0}, q[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        uint64_t a = (rem << 32) | (limbs[t] >> 32);
-        uint64_t qa = a / j;
-        rem = a % j;
-        uint64_t b = (rem << 32) | (limbs[t] & 0xffffffffull);
-        uint64_t qb = b / j;
-        rem = b % j;
-        q[t] = (qa << 32) | qb;
-    }
-    hi = q[0];
-    lo = q[1];
-    return q2 != 0;
-}
-
 __global__ void k_binomial(ulonglong2 *c, int32_t *n_ovf, int32_t nmax) {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= nmax; n += (int64_t)gridDim.x * blockDim.x) {
         uint64_t lo = 1, hi = 0;
