@@ -273,19 +273,26 @@ def main():
         e2e = {"value": em / n_counts, "unit": "ms", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 16 * len(pqs)}
 
-    # ---- roofline of the dominant kernel (the enumeration) against measured HBM
+    # ---- roofline of the dominant kernel (the enumeration).  ncu shows it bound
+    # by instruction issue on the integer pipe with its bitmap rows resident in
+    # L1/L2 (DRAM traffic is a few hundred MB per launch against terabytes of
+    # words), so the roofline is ALU: each bitmap word the kernel loads costs one
+    # AND, one POPC and one ADD; the peak is 128 integer lanes per SM per clock.
     peaks = _peaks()
-    hbm = peaks.get("hbm_gbs")
     roof = None
     if enum_launches:
-        bytes_per_launch = 4.0 * enum_words / enum_launches
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_tops = n_sms * 128 * sm_max * 1e6 / 1e12
+        ops_per_launch = 3.0 * enum_words / enum_launches
         ms_per_launch = enum_ms / enum_launches
-        achieved = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
-        peak = hbm if hbm else 6800.0
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _ncu_traffic(), "kernel": "k_enumerate",
-                "peak_source": "measured" if hbm else "fallback",
-                "algorithmic_bytes_per_launch": bytes_per_launch, "ms_per_launch": ms_per_launch}
+        achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": _ncu_traffic(), "kernel": "k_enumerate",
+                "peak_source": f"derived: {n_sms} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz max SM clock",
+                "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 3,
+                "words_per_launch": enum_words / enum_launches, "launches": enum_launches,
+                "ms_per_launch": ms_per_launch}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
