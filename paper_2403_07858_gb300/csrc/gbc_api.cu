@@ -320,13 +320,17 @@ extern "C" gbc_status gbc_load_graph_device(gbc_ctx_t ctx, int32_t nU, int32_t n
 // the count pipeline
 static int pick_anchor(const gbc_graph_s *g, int p, int q) {
     // A side of size 1 needs no search at all; otherwise enumerate the smaller
-    // set.  For p == q anchor the side with the lighter degree tail (smaller
-    // sum of C(deg, 2) over its own vertices): its roots have narrower C_R rows
-    // and fewer deep subtrees, which dominate the cost from p = q = 4 on.
+    // set.  For p == q the cost has two regimes.  Up to p = q = 4 the 2-hop
+    // candidate stage dominates: its wedges pass through the other side, so
+    // anchor U costs sum_v C(deg v, 2) and anchor V sum_u C(deg u, 2); take the
+    // cheaper.  From p = q = 5 on the deep subtrees dominate: anchor the side
+    // with the lighter degree tail (smaller sum of C(deg, 2) over its own
+    // vertices), whose roots have narrower C_R rows and sparser compatibility.
     if (p == 1) return GBC_ANCHOR_U;
     if (q == 1) return GBC_ANCHOR_V;
     if (p < q) return GBC_ANCHOR_U;
     if (q < p) return GBC_ANCHOR_V;
+    if (p <= 4) return g->wedgesV <= g->wedgesU ? GBC_ANCHOR_U : GBC_ANCHOR_V;
     return g->wedgesU <= g->wedgesV ? GBC_ANCHOR_U : GBC_ANCHOR_V;
 }
 
