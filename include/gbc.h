@@ -193,6 +193,21 @@ gbc_status gbc_count_p2_noalloc(int32_t nU, int32_t nV, const int32_t *offU_d, c
                                 const int32_t *offV_d, const int32_t *adjV_d, int q, void *stream,
                                 gbc_u128 *out);
 
+/*
+ * gbc_count_batch -- many counts, possibly on different graphs of this context,
+ * in one pipeline: every stage runs for all jobs before the host waits, and the
+ * enumeration (Alg. 1's search below the roots' children, Sec. IV) of all jobs
+ * is one persistent launch over their concatenated level-2 work units.
+ *   graphs[n], p[n], q[n]: host arrays; graphs must belong to ctx;
+ *   out[n]: host, the count of job i when per_job[i] == GBC_OK;
+ *   per_job[n]: host, each job's status (GBC_ERR_ARG, _OOM, _OVERFLOW, ...).
+ * Returns GBC_OK when the batch ran (check per_job), GBC_ERR_ARG for null
+ * arrays, GBC_ERR_CUDA if the device failed.  Scratch is granted in waves that
+ * fit the context's budget.
+ */
+gbc_status gbc_count_batch(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const int *p, const int *q,
+                           gbc_u128 *out, gbc_status *per_job);
+
 /* Human-readable text of a status, and the calling thread's last error. */
 const char *gbc_status_string(gbc_status s);
 const char *gbc_last_error(void);

@@ -113,6 +113,9 @@ SIGNATURES = {
                                           ctypes.POINTER(U128), ctypes.POINTER(U128)]),
     "gbc_count_p2_noalloc": (ctypes.c_int, [_i32, _i32, _vp, _vp, _vp, _vp, ctypes.c_int, _vp,
                                             ctypes.POINTER(U128)]),
+    "gbc_count_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(U128),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbc_last_error": (ctypes.c_char_p, []),
 }
@@ -250,6 +253,24 @@ class Context:
             ptrs = [ctypes.c_void_p(p) for _, p in keep]
             _check(lib.gbc_load_graph(self._h, n_u, n_v, *ptrs, ctypes.byref(h)), "gbc_load_graph")
         return Graph(self, h.value)
+
+    def count_batch(self, graphs, ps, qs):
+        """Counts of (graphs[i], ps[i], qs[i]) in one batched pipeline; returns a list
+        whose entries are ints, or GbcError instances for jobs that failed."""
+        n = len(graphs)
+        hs = (ctypes.c_void_p * max(1, n))(*[g._h.value for g in graphs])
+        pa = (ctypes.c_int * max(1, n))(*ps)
+        qa = (ctypes.c_int * max(1, n))(*qs)
+        out = (U128 * max(1, n))()
+        st = (ctypes.c_int * max(1, n))()
+        _check(load_library().gbc_count_batch(self._h, n, hs, pa, qa, out, st), "gbc_count_batch")
+        res = []
+        for i in range(n):
+            if st[i] == GBC_OK:
+                res.append(out[i].value())
+            else:
+                res.append(GbcError(st[i], load_library().gbc_status_string(st[i]).decode()))
+        return res
 
     def load(self, g) -> Graph:
         """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""

@@ -356,6 +356,261 @@ struct Timer {
     }
 };
 
+// Small per-count device state: the u128 sum, status, tier sizes, work
+// counters, totals of the per-root scans and the enumeration's word count.
+struct Small {
+    unsigned long long acc[2];
+    int64_t totals[3];
+    uint32_t status;
+    int32_t tier_count[3];
+    int32_t omega_max[3];
+    int32_t queues[8];
+    int32_t n_units;
+    int32_t cand_max;
+    unsigned long long deadline;
+    unsigned long long enum_words;
+};
+
+// One count of a (possibly one-element) batch.
+struct Job {
+    gbc_graph_s *g = nullptr;
+    int p = 0, q = 0, anchor = 0;
+    unsigned long long *per_root = nullptr;
+    CountArgs a;
+    Small h;
+    bool trivial = false;
+    gbc_status st = GBC_OK;
+    char err[256] = "";
+    void set_error(gbc_status s, const char *fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(err, sizeof err, fmt, ap);
+        va_end(ap);
+        st = s;
+    }
+};
+
+// Runs every job of the batch phase by phase on the context's stream: one host
+// synchronisation after the root classification, one after the per-root
+// scans, and one at the end, whatever the number of jobs.  The enumeration of
+// all jobs with |L| >= 4 is one persistent launch (a job table on the device).
+// Per-job scratch is granted in waves that fit the context's budget.
+// Returns a batch-level error (CUDA failure); per-job outcomes are in job.st.
+static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_count_options *opt, bool want_stats,
+                           Timer &tm, SearchStats *hs_out) {
+    cudaStream_t st = ctx->stream;
+    const int n = (int)jobs.size();
+    Scratch sc(st);
+    Small *d_small = nullptr;
+    CK(sc.get(&d_small, n));
+    CK(cudaMemsetAsync(d_small, 0, sizeof(Small) * n, st));
+    SearchStats *d_stats = nullptr;
+    if (want_stats) {
+        CK(sc.get(&d_stats, 1));
+        CK(cudaMemsetAsync(d_stats, 0, sizeof(SearchStats), st));
+    }
+    std::vector<Small> hs(n);
+    tm.mark(0, st);
+    // ---- phase 0: arguments; single-vertex sets finish here
+    for (int i = 0; i < n; ++i) {
+        Job &J = jobs[i];
+        gbc_graph_s *g = J.g;
+        CountArgs &a = J.a;
+        memset(&a, 0, sizeof a);
+        if (J.anchor == GBC_ANCHOR_U) {
+            a.g = SideView{g->nU, g->nV, g->offU, g->adjU, g->offV, g->adjV_byU, g->mirrorU, g->degU, g->maxdegU};
+            a.k = J.p;
+            a.kq = J.q;
+        } else {
+            a.g = SideView{g->nV, g->nU, g->offV, g->adjV, g->offU, g->adjU_byV, g->mirrorV, g->degV, g->maxdegV};
+            a.k = J.q;
+            a.kq = J.p;
+        }
+        a.binom = BinomTable{g->binom, g->n_ovf, g->binom_nmax};
+        Small *s = d_small + i;
+        a.acc = s->acc;
+        a.status = &s->status;
+        a.tier_count = s->tier_count;
+        a.omega_max = s->omega_max;
+        a.queues = s->queues;
+        a.n_units = &s->n_units;
+        a.cand_max = &s->cand_max;
+        a.deadline = &d_small[0].deadline;  // one deadline for the batch
+        a.enum_words = &s->enum_words;
+        a.stats = d_stats;
+        a.per_root = J.per_root;
+        J.trivial = (a.k > a.g.nA) || (a.kq > a.g.maxdegA) || a.g.nA == 0;
+        if (!J.trivial && a.k == 1) CK(launch_single_vertex_sets(a, st));
+    }
+    if (opt && opt->time_limit_ms > 0)
+        CK(launch_set_deadline(&d_small[0].deadline, (unsigned long long)opt->time_limit_ms * 1000000ull, st));
+    auto active = [&](const Job &J) { return J.st == GBC_OK && !J.trivial && J.a.k >= 2; };
+    // ---- phase 1: oriented wedge counts and root tiers
+    bool any = false;
+    for (Job &J : jobs) {
+        if (!active(J)) continue;
+        const int64_t nA = J.a.g.nA;
+        CK(sc.get(&J.a.omega, nA));
+        CK(sc.get(&J.a.tier_list, 3 * nA));
+        CK(sc.get(&J.a.cand_count, nA));
+        CK(launch_root_omega(J.a, st));
+        any = true;
+    }
+    if (any) {
+        CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    // ---- phase 2: candidates (pass A) and, for |L| >= 3, the per-root offsets
+    any = false;
+    for (int i = 0; i < n; ++i) {
+        Job &J = jobs[i];
+        if (!active(J)) continue;
+        CountArgs &a = J.a;
+        const Small &h = hs[i];
+        if (h.tier_count[2] > 0) {
+            if (h.omega_max[2] > (1 << 28)) {
+                J.set_error(GBC_ERR_OOM, "gbc_count: a root has %d oriented wedges (limit 2^28)", h.omega_max[2]);
+                continue;
+            }
+            int64_t slots = 32, sortcap = 1;
+            while (slots < 2 * (int64_t)h.omega_max[2]) slots <<= 1;
+            while (sortcap < h.omega_max[2]) sortcap <<= 1;
+            a.slab_words = 2 * slots + 2 * sortcap;
+            const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
+            CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
+        }
+        CK(launch_candidates(a, false, h.tier_count, ctx->n_sms, st));
+        if (a.k >= 3) {
+            const int64_t nA = a.g.nA;
+            int64_t *cand_off, *r_off, *s_off, *tmp;
+            CK(sc.get(&cand_off, nA + 1));
+            CK(sc.get(&r_off, nA + 1));
+            CK(sc.get(&s_off, nA + 1));
+            CK(sc.get(&tmp, 3 * ((nA + 1) / 2048 + 2)));
+            a.cand_off = cand_off;
+            a.r_off = r_off;
+            a.s_off = s_off;
+            CK(launch_root_offsets(a, cand_off, r_off, s_off, tmp, d_small[i].totals, st));
+            any = true;
+        }
+    }
+    tm.mark(1, st);
+    if (any) {
+        CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    // ---- phase 3 (in waves): bitmap rows, pairwise rows, enumeration
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i) {
+        Job &J = jobs[i];
+        if (!active(J) || J.a.k < 3) continue;
+        J.a.n_cand = hs[i].totals[0];
+        if (J.a.n_cand == 0) continue;
+        if (J.a.n_cand >= INT32_MAX) {
+            J.set_error(GBC_ERR_OOM, "gbc_count: %lld candidates exceed one launch", (long long)J.a.n_cand);
+            continue;
+        }
+        todo.push_back(i);
+    }
+    auto need_of = [&](int i) {
+        const Small &h = hs[i];
+        const Job &J = jobs[i];
+        return (size_t)h.totals[0] * 12 + (size_t)h.totals[1] * 4 + (size_t)h.totals[2] * 4 +
+               (size_t)std::max<int64_t>(J.g->nE, 1) * 8;
+    };
+    size_t pos = 0;
+    while (pos < todo.size()) {
+        Scratch wave_sc(st);
+        std::vector<int> wave;
+        size_t used = sc.bytes;
+        for (; pos < todo.size(); ++pos) {
+            const int i = todo[pos];
+            const size_t need = need_of(i);
+            if (used + need > ctx->budget) {
+                if (wave.empty()) {
+                    jobs[i].set_error(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need,
+                                      ctx->budget);
+                    continue;
+                }
+                break;
+            }
+            used += need;
+            wave.push_back(i);
+        }
+        std::vector<CountArgs> enum_jobs;
+        int max_wr = 2, max_wl = 2, max_k = 4;
+        for (int i : wave) {
+            CountArgs &a = jobs[i].a;
+            const Small &h = hs[i];
+            const int64_t nE = std::max<int64_t>(jobs[i].g->nE, 1);
+            CK(wave_sc.get(&a.poscnt, nE));
+            CK(wave_sc.get(&a.posmap, nE));
+            CK(cudaMemsetAsync(a.poscnt, 0, (size_t)nE * 4, st));
+            CK(wave_sc.get(&a.cand, a.n_cand));
+            CK(wave_sc.get(&a.cand_root, a.n_cand));
+            CK(wave_sc.get(&a.R, h.totals[1]));
+            CK(cudaMemsetAsync(a.R, 0, std::max<int64_t>(h.totals[1], 1) * 4, st));
+            if (a.k >= 4) {
+                CK(wave_sc.get(&a.S, h.totals[2]));
+                CK(cudaMemsetAsync(a.S, 0, std::max<int64_t>(h.totals[2], 1) * 4, st));
+                CK(wave_sc.get(&a.units, a.n_cand));
+            }
+            CK(launch_candidates(a, true, h.tier_count, ctx->n_sms, st));
+        }
+        tm.mark(1, st);
+        for (int i : wave) {
+            CountArgs &a = jobs[i].a;
+            const Small &h = hs[i];
+            CK(launch_pairs(a, ctx->n_sms, st));
+            if (a.k >= 4) {
+                enum_jobs.push_back(a);
+                max_wr = std::max(max_wr, (int)row_stride(a.g.maxdegA));
+                max_wl = std::max(max_wl, (std::max(h.cand_max, 1) + 31) / 32);
+                max_k = std::max(max_k, a.k);
+            }
+        }
+        tm.mark(2, st);
+        if (!enum_jobs.empty()) {
+            CountArgs *d_jobs = nullptr;
+            int64_t *d_prefix = nullptr;
+            int32_t *d_queue = nullptr;
+            CK(wave_sc.get(&d_jobs, enum_jobs.size()));
+            CK(wave_sc.get(&d_prefix, enum_jobs.size() + 1));
+            CK(wave_sc.get(&d_queue, 1));
+            CK(cudaMemsetAsync(d_queue, 0, 4, st));
+            CK(cudaMemcpyAsync(d_jobs, enum_jobs.data(), sizeof(CountArgs) * enum_jobs.size(),
+                               cudaMemcpyHostToDevice, st));
+            CK(launch_enumerate(d_jobs, (int)enum_jobs.size(), d_prefix, d_queue, want_stats,
+                                opt ? opt->enum_warps : 0, max_wr, max_wl, max_k, ctx->n_sms, st));
+            // the job table is read by the launch: keep the host copy alive until it has run
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    tm.mark(3, st);
+    CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
+    if (d_stats && hs_out) CK(cudaMemcpyAsync(hs_out, d_stats, sizeof(SearchStats), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    const uint32_t batch_status = hs[0].status;
+    for (int i = 0; i < n; ++i) {
+        Job &J = jobs[i];
+        J.h = hs[i];
+        if (J.st != GBC_OK) continue;
+        if ((J.h.status | batch_status) & kStTimeout)
+            J.set_error(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its %d ms time limit", J.p, J.q,
+                        opt ? opt->time_limit_ms : 0);
+        else if (J.h.status & kStOverflow)
+            J.set_error(GBC_ERR_OVERFLOW, "gbc_count: (%d,%d) count exceeds 2^128-1", J.p, J.q);
+        else if (J.h.status)
+            J.set_error(GBC_ERR_CUDA, "gbc_count: device status 0x%x", J.h.status);
+    }
+    return GBC_OK;
+}
+
+static int resolve_anchor(const gbc_graph_s *g, int p, int q, int requested) {
+    return requested ? requested : pick_anchor(g, p, q);
+}
+
 static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_options *opt, gbc_u128 *out,
                              gbc_count_info *info, int force_anchor, unsigned long long *per_root_dev) {
     if (!g || (!out && !per_root_dev)) return fail(GBC_ERR_ARG, "gbc_count: null argument");
@@ -364,177 +619,92 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
     gbc_ctx_s *ctx = g->ctx;
     std::lock_guard<std::mutex> lk(ctx->mu);
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
-    gbc_count_info inf;
-    memset(&inf, 0, sizeof inf);
-    int anchor = force_anchor ? force_anchor : (opt && opt->anchor ? opt->anchor : pick_anchor(g, p, q));
+    const int anchor = resolve_anchor(g, p, q, force_anchor ? force_anchor : (opt ? opt->anchor : 0));
     if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_count: bad anchor %d", anchor);
     const bool want_stats = opt && opt->collect_stats;
-
-    CountArgs a;
-    memset(&a, 0, sizeof a);
-    if (anchor == GBC_ANCHOR_U) {
-        a.g = SideView{g->nU, g->nV, g->offU, g->adjU, g->offV, g->adjV_byU, g->mirrorU, g->degU, g->maxdegU};
-        a.k = p;
-        a.kq = q;
-    } else {
-        a.g = SideView{g->nV, g->nU, g->offV, g->adjV, g->offU, g->adjU_byV, g->mirrorV, g->degV, g->maxdegV};
-        a.k = q;
-        a.kq = p;
-    }
-    a.binom = BinomTable{g->binom, g->n_ovf, g->binom_nmax};
-    inf.anchor_used = anchor;
-    inf.set_size = a.k;
-    gbc_u128 result{0, 0};
-
+    std::vector<Job> jobs(1);
+    jobs[0].g = g;
+    jobs[0].p = p;
+    jobs[0].q = q;
+    jobs[0].anchor = anchor;
+    jobs[0].per_root = per_root_dev;
     t_launches = 0;
     Timer tm;
     tm.init(info != nullptr);
-    tm.mark(0, st);
-    Scratch sc(st);
-    // small device state: acc[2], status, tier_count[3], omega_max[3], queues[8], n_units, cand_max, totals[3]
-    struct Small {
-        unsigned long long acc[2];
-        int64_t totals[3];
-        uint32_t status;
-        int32_t tier_count[3];
-        int32_t omega_max[3];
-        int32_t queues[8];
-        int32_t n_units;
-        int32_t cand_max;
-        unsigned long long deadline;
-        unsigned long long enum_words;
-    };
-    Small *d_small = nullptr;
-    CK(sc.get(&d_small, 1));
-    CK(cudaMemsetAsync(d_small, 0, sizeof(Small), st));
-    SearchStats *d_stats = nullptr;
-    if (want_stats) {
-        CK(sc.get(&d_stats, 1));
-        CK(cudaMemsetAsync(d_stats, 0, sizeof(SearchStats), st));
-    }
-    a.acc = d_small->acc;
-    a.status = &d_small->status;
-    a.tier_count = d_small->tier_count;
-    a.omega_max = d_small->omega_max;
-    a.queues = d_small->queues;
-    a.n_units = &d_small->n_units;
-    a.cand_max = &d_small->cand_max;
-    a.deadline = &d_small->deadline;
-    a.enum_words = &d_small->enum_words;
-    if (opt && opt->time_limit_ms > 0)
-        CK(launch_set_deadline(a.deadline, (unsigned long long)opt->time_limit_ms * 1000000ull, st));
-    a.stats = d_stats;
-    a.per_root = per_root_dev;
-    Small h{};
-    const bool trivial = (a.k > a.g.nA) || (a.kq > a.g.maxdegA) || a.g.nA == 0;
-    if (!trivial) {
-        if (a.k == 1) {
-            CK(launch_single_vertex_sets(a, st));
-        } else {
-            const int64_t nA = a.g.nA;
-            CK(sc.get(&a.omega, nA));
-            CK(sc.get(&a.tier_list, 3 * nA));
-            CK(sc.get(&a.cand_count, nA));
-            CK(launch_root_omega(a, st));
-            CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            // tier-2 slabs: hash table of next_pow2(2*omega) slots + sort buffer
-            if (h.tier_count[2] > 0) {
-                if (h.omega_max[2] > (1 << 28))
-                    return fail(GBC_ERR_OOM, "gbc_count: a root has %d oriented wedges (limit 2^28)", h.omega_max[2]);
-                int64_t slots = 32, sortcap = 1;
-                while (slots < 2 * (int64_t)h.omega_max[2]) slots <<= 1;
-                while (sortcap < h.omega_max[2]) sortcap <<= 1;
-                a.slab_words = 2 * slots + 2 * sortcap;
-                const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
-                CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
-            }
-            CK(launch_candidates(a, false, h.tier_count, ctx->n_sms, st));
-            tm.mark(1, st);
-            if (a.k >= 3) {
-                int64_t *cand_off, *r_off, *s_off, *tmp;
-                CK(sc.get(&cand_off, nA + 1));
-                CK(sc.get(&r_off, nA + 1));
-                CK(sc.get(&s_off, nA + 1));
-                CK(sc.get(&tmp, 3 * ((nA + 1) / 2048 + 2)));
-                a.cand_off = cand_off;
-                a.r_off = r_off;
-                a.s_off = s_off;
-                CK(launch_root_offsets(a, cand_off, r_off, s_off, tmp, d_small->totals, st));
-                CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                a.n_cand = h.totals[0];
-                inf.candidates = h.totals[0];
-                if (a.n_cand >= INT32_MAX) return fail(GBC_ERR_OOM, "gbc_count: %lld candidates exceed one launch", (long long)a.n_cand);
-                const size_t need = (size_t)h.totals[0] * 12 + (size_t)h.totals[1] * 4 + (size_t)h.totals[2] * 4;
-                if (need + sc.bytes > ctx->budget)
-                    return fail(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need, ctx->budget);
-                if (a.n_cand > 0) {
-                    const int64_t nE = std::max<int64_t>(g->nE, 1);
-                    CK(sc.get(&a.poscnt, nE));
-                    CK(sc.get(&a.posmap, nE));
-                    CK(cudaMemsetAsync(a.poscnt, 0, (size_t)nE * 4, st));
-                    CK(sc.get(&a.cand, a.n_cand));
-                    CK(sc.get(&a.cand_root, a.n_cand));
-                    CK(sc.get(&a.R, h.totals[1]));
-                    CK(cudaMemsetAsync(a.R, 0, std::max<int64_t>(h.totals[1], 1) * 4, st));
-                    if (a.k >= 4) {
-                        CK(sc.get(&a.S, h.totals[2]));
-                        CK(cudaMemsetAsync(a.S, 0, std::max<int64_t>(h.totals[2], 1) * 4, st));
-                        CK(sc.get(&a.units, a.n_cand));
-                    }
-                    CK(launch_candidates(a, true, h.tier_count, ctx->n_sms, st));
-                    tm.mark(1, st);
-                    CK(launch_pairs(a, ctx->n_sms, st));
-                    tm.mark(2, st);
-                    if (a.k >= 4) {
-                        // stack layout from the largest row widths of this count
-                        const int max_wr = row_stride(a.g.maxdegA);
-                        const int max_wl = (std::max(h.cand_max, 1) + 31) / 32;
-                        CK(launch_enumerate(a, opt ? opt->enum_warps : 0, max_wr, max_wl, ctx->n_sms, st));
-                    }
-                }
-            }
-            inf.scratch_bytes = (int64_t)sc.bytes;
-        }
-    }
-    tm.mark(3, st);
-    CK(cudaMemcpyAsync(&h, d_small, sizeof(Small), cudaMemcpyDeviceToHost, st));
     SearchStats hs;
     memset(&hs, 0, sizeof hs);
-    if (d_stats) CK(cudaMemcpyAsync(&hs, d_stats, sizeof hs, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
-    if (h.status & kStTimeout) return fail(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its %d ms time limit", p, q,
-                                           opt ? opt->time_limit_ms : 0);
-    if (h.status & kStOverflow) return fail(GBC_ERR_OVERFLOW, "gbc_count: (%d,%d) count exceeds 2^128-1", p, q);
-    if (h.status) return fail(GBC_ERR_CUDA, "gbc_count: device status 0x%x", h.status);
-    result.lo = h.acc[0];
-    result.hi = h.acc[1];
+    gbc_status s = run_jobs(ctx, jobs, opt, want_stats, tm, &hs);
+    if (s != GBC_OK) return s;
+    Job &J = jobs[0];
+    if (J.st != GBC_OK) return fail(J.st, "%s", J.err);
     if (info) {
+        gbc_count_info inf;
+        memset(&inf, 0, sizeof inf);
+        inf.anchor_used = anchor;
+        inf.set_size = J.a.k;
         inf.roots = (int64_t)hs.roots;
-        if (!inf.candidates) inf.candidates = (int64_t)hs.cands;
-        inf.units = want_stats ? (int64_t)hs.units : h.n_units;
+        inf.candidates = J.h.totals[0] ? J.h.totals[0] : (int64_t)hs.cands;
+        inf.units = want_stats ? (int64_t)hs.units : J.h.n_units;
         for (int l = 0; l <= GBC_MAX_PQ; ++l) {
             inf.evals[l] = (int64_t)hs.evals[l];
             inf.passed[l] = (int64_t)hs.passed[l];
         }
         inf.words_r = (int64_t)hs.words_r;
         inf.words_l = (int64_t)hs.words_l;
-        if (!trivial && a.k >= 2) {
+        if (!J.trivial && J.a.k >= 2) {
             inf.ms_candidates = tm.between(0, 1);
-            if (a.k >= 3 && a.n_cand > 0) {
+            if (J.a.k >= 3 && J.a.n_cand > 0) {
                 inf.ms_pairs = tm.between(1, 2);
-                inf.ms_enumerate = a.k >= 4 ? tm.between(2, 3) : 0.f;
+                inf.ms_enumerate = J.a.k >= 4 ? tm.between(2, 3) : 0.f;
             }
         }
         inf.ms_total = tm.between(0, 3);
-        inf.enum_words = (int64_t)h.enum_words;
+        inf.enum_words = (int64_t)J.h.enum_words;
         inf.launches = t_launches;
         *info = inf;
     }
-    if (out) *out = result;
+    if (out) {
+        out->lo = J.h.acc[0];
+        out->hi = J.h.acc[1];
+    }
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_count_batch(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const int *p,
+                                      const int *q, gbc_u128 *out, gbc_status *per_job) {
+    if (!ctx || n < 0 || (n > 0 && (!graphs || !p || !q || !out || !per_job)))
+        return fail(GBC_ERR_ARG, "gbc_count_batch: null argument");
+    if (n == 0) return GBC_OK;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<Job> jobs;
+    std::vector<int> slot;
+    jobs.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        per_job[i] = GBC_OK;
+        out[i] = gbc_u128{0, 0};
+        if (!graphs[i] || graphs[i]->ctx != ctx) { per_job[i] = GBC_ERR_ARG; continue; }
+        if (p[i] < 1 || q[i] < 1 || p[i] > GBC_MAX_PQ || q[i] > GBC_MAX_PQ) { per_job[i] = GBC_ERR_ARG; continue; }
+        Job J;
+        J.g = graphs[i];
+        J.p = p[i];
+        J.q = q[i];
+        J.anchor = resolve_anchor(graphs[i], p[i], q[i], 0);
+        jobs.push_back(J);
+        slot.push_back(i);
+    }
+    t_launches = 0;
+    Timer tm;
+    tm.init(false);
+    if (!jobs.empty()) {
+        gbc_status s = run_jobs(ctx, jobs, nullptr, false, tm, nullptr);
+        if (s != GBC_OK) return s;
+    }
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        per_job[slot[j]] = jobs[j].st;
+        if (jobs[j].st == GBC_OK) out[slot[j]] = gbc_u128{jobs[j].h.acc[0], jobs[j].h.acc[1]};
+        else fail(jobs[j].st, "%s", jobs[j].err);
+    }
     return GBC_OK;
 }
 

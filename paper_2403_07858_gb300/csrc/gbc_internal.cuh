@@ -249,7 +249,10 @@ cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tie
 cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *r_off, int64_t *s_off,
                                 int64_t *tmp, int64_t *totals, cudaStream_t st);
 cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st);
-cudaError_t launch_enumerate(const CountArgs &a, int n_warps, int max_wr, int max_wl, int n_sms,
-                             cudaStream_t st);
+// One persistent launch over the level-2 units of n_jobs counts (d_jobs: a
+// device array of their CountArgs).  d_prefix: n_jobs + 1 int64 of scratch;
+// d_queue: a zeroed int32 work counter.
+cudaError_t launch_enumerate(const CountArgs *d_jobs, int n_jobs, int64_t *d_prefix, int32_t *d_queue, bool stats,
+                             int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms, cudaStream_t st);
 
 }  // namespace gbc

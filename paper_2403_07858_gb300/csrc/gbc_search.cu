@@ -768,15 +768,26 @@ constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never
 
 template <bool STATS>
 __global__ void __launch_bounds__(256)
-k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
+k_enumerate(const CountArgs *jobs, int n_jobs, const int64_t *prefix, int32_t *queue, EnumLayout lay,
+            uint32_t *gstack) {
     extern __shared__ __align__(16) uint32_t smem_stack[];
     __shared__ ulonglong2 s_binom[kSmemBinom];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int k = a.k, kq = a.kq;
-    for (int n = threadIdx.x; n < kSmemBinom; n += blockDim.x)
-        s_binom[n] = n <= a.binom.nmax ? a.binom.c[(size_t)kq * (a.binom.nmax + 1) + n] : make_ulonglong2(0, 0);
+    // C(n, kq0) for n < 256 in shared memory, for the first job's kq (any job
+    // with another kq reads its own table); binomials do not depend on the graph
+    const int kq0 = jobs[0].kq;
+    for (int n = threadIdx.x; n < kSmemBinom; n += blockDim.x) {
+        bool o = false;
+        uint64_t lo = 1, hi = 0;
+        for (int jj = 1; jj <= kq0 && !o; ++jj) {
+            if (jj > n) { lo = 0; hi = 0; break; }
+            o = mul_div_small(lo, hi, (uint32_t)(n - jj + 1), (uint32_t)jj);
+        }
+        s_binom[n] = make_ulonglong2(lo, hi);
+    }
     __syncthreads();
+    const CountArgs &a0 = jobs[0];  // holds the batch-wide deadline and status
     uint32_t *wbase = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
                              : smem_stack + (int64_t)wib * lay.warp_words();
     uint4 *CRY = reinterpret_cast<uint4 *>(wbase);              // C_R of each lane's leaf parent
@@ -790,17 +801,25 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     auto CL = [&](int lv) { return base + (int64_t)lv * lay.level_words() + lay.wr; };
     auto XS = [&](int lv) { return reinterpret_cast<int32_t *>(base + (int64_t)lv * lay.level_words() + lay.wr + lay.wl); };
 
-    u128 acc = 0;
     bool ovf = false;
-    unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
     unsigned long long st_evals[2] = {0, 0}, st_passed[2] = {0, 0}, st_wr = 0, st_wl = 0;
-    const int n_units = *a.n_units;
+    const int64_t total_units = prefix[n_jobs];
     while (true) {
-        int uidx = 0;
-        if (lane == 0) uidx = atomicAdd(a.queues + 7, 1);
-        uidx = __shfl_sync(kFull, uidx, 0);
-        if (uidx >= n_units || past_deadline(a)) break;
-        const int64_t gidx = a.units[uidx];
+        int64_t guidx = 0;
+        if (lane == 0) guidx = atomicAdd(queue, 1);
+        guidx = __shfl_sync(kFull, (long long)guidx, 0);
+        if (guidx >= total_units || past_deadline(a0)) break;
+        // the job of this unit: the last job whose first unit is at or before it
+        int lo_j = 0, hi_j = n_jobs - 1;
+        while (lo_j < hi_j) {
+            const int mid = (lo_j + hi_j + 1) >> 1;
+            if (prefix[mid] <= guidx) lo_j = mid; else hi_j = mid - 1;
+        }
+        const CountArgs &a = jobs[lo_j];
+        const int k = a.k, kq = a.kq;
+        const bool smem_binom = kq == kq0;
+        unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
+        const int64_t gidx = a.units[guidx - prefix[lo_j]];
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
         const int64_t c = a.cand_count[r];
@@ -823,7 +842,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
         int lv = 0;
         unsigned batches = 0;
         while (true) {
-            if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
+            if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a0), 0)) break;
             const uint32_t dm = dmask[lv];
             if (dm != 0) {
                 const int t = __ffs(dm) - 1;
@@ -943,7 +962,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
                                         if (STATS) { st_evals[1] += 1; st_wr += WRm; }
                                         if (n >= kq) {
                                             if (STATS) st_passed[1] += 1;
-                                            if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                            if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
                                             else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
                                         }
                                     }
@@ -967,7 +986,7 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
                             if (STATS) { st_evals[1] += 1; st_wr += WRm; }
                             if (n >= kq) {
                                 if (STATS) st_passed[1] += 1;
-                                if (n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
                                 else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
                             }
                         }
@@ -1007,21 +1026,21 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
             if (lane == 0) dmask[lv] = dmb;
             __syncwarp();
         }
-        if (a.per_root) {
-            u128 s = warp_sum_u128(unit_acc, ovf);
-            if (lane == 0) atomic_add_u128(a.per_root + 2 * (int64_t)r, s, a.status);
-        }
-        add_u128(acc, unit_acc, ovf);
-    }
-    acc = warp_sum_u128(acc, ovf);
+        // the unit's sum goes to its job (and to its root when split by root)
+        const u128 s = warp_sum_u128(unit_acc, ovf);
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
-    if (lane == 0) {
-        if (ovf) atomicOr(a.status, kStOverflow);
-        atomic_add_u128(a.acc, acc, a.status);
-        atomicAdd(a.enum_words, words);
+        for (int o = 16; o >= 1; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
+        if (lane == 0) {
+            if (ovf) atomicOr(a.status, kStOverflow);
+            atomic_add_u128(a.acc, s, a.status);
+            if (a.per_root) atomic_add_u128(a.per_root + 2 * (int64_t)r, s, a.status);
+            atomicAdd(a.enum_words, words);
+        }
+        ovf = false;
     }
     if (STATS) {
+        const CountArgs &a = a0;  // statistics are kept for single-job launches
+        const int k = a.k;
         // the last two levels were counted per lane
         atomicAdd(&a.stats->evals[k - 1], st_evals[0]);
         atomicAdd(&a.stats->evals[k], st_evals[1]);
@@ -1032,9 +1051,22 @@ k_enumerate(CountArgs a, EnumLayout lay, uint32_t *gstack) {
     }
 }
 
-cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, int max_wl, int n_sms,
-                             cudaStream_t st) {
-    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, a.k - 3)};
+__global__ void k_unit_prefix(const CountArgs *jobs, int n_jobs, int64_t *prefix) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t t = 0;
+        for (int i = 0; i < n_jobs; ++i) {
+            prefix[i] = t;
+            t += *jobs[i].n_units;
+        }
+        prefix[n_jobs] = t;
+    }
+}
+
+cudaError_t launch_enumerate(const CountArgs *d_jobs, int n_jobs, int64_t *d_prefix, int32_t *d_queue, bool stats,
+                             int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms, cudaStream_t st) {
+    k_unit_prefix<<<1, 32, 0, st>>>(d_jobs, n_jobs, d_prefix);
+    ++t_launches;
+    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3)};
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;
     const size_t smem = per_warp * warps_per_cta;
@@ -1044,19 +1076,19 @@ cudaError_t launch_enumerate(const CountArgs &a, int n_warps_hint, int max_wr, i
     uint32_t *gstack = nullptr;
     cudaError_t err;
     if (use_smem) {
-        auto kern = a.stats ? k_enumerate<true> : k_enumerate<false>;
+        auto kern = stats ? k_enumerate<true> : k_enumerate<false>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_cta, smem);
         if (n_warps_hint <= 0) grid = n_sms * std::max(1, per_sm);
-        kern<<<grid, 32 * warps_per_cta, smem, st>>>(a, lay, nullptr);
+        kern<<<grid, 32 * warps_per_cta, smem, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, nullptr);
         ++t_launches;
     } else {
         err = cudaMallocAsync(reinterpret_cast<void **>(&gstack), per_warp * warps_per_cta * grid, st);
         if (err != cudaSuccess) return err;
-        if (a.stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
-        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(a, lay, gstack);
+        if (stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, gstack);
+        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, gstack);
         ++t_launches;
         err = cudaGetLastError();
         cudaFreeAsync(gstack, st);

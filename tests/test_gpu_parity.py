@@ -237,3 +237,32 @@ def test_disjoint_union_additive_gpu(gpu_ctx):
     u = bipgen.disjoint_union(a, b, c)
     for p, q in [(3, 3), (4, 4)]:
         assert _gpu_count(gpu_ctx, u, p, q) == sum(_gpu_count(gpu_ctx, x, p, q) for x in (a, b, c))
+
+
+def test_batch_equals_single_counts(gpu_ctx):
+    """gbc_count_batch: one pipeline and one enumeration launch for many jobs on
+    several graphs; every job equals its own gbc_count, errors stay per job."""
+    import paper_2403_07858_gb300 as gbc
+    graphs = [bipgen.workload_small(), _all_tiers_graph(), bipgen.complete(20, 30),
+              bipgen.tiny_random(4, 9, 11, 0.5), bipgen.from_edges(3, 3, [], []), bipgen.complete(16, 1000)]
+    hs = [gpu_ctx.load(g) for g in graphs]
+    jobs = []
+    for gi in range(4):
+        for p, q in [(1, 2), (2, 2), (3, 3), (4, 4), (2, 5), (5, 2), (4, 6), (6, 3)]:
+            jobs.append((gi, p, q))
+    jobs += [(4, 2, 2), (5, 8, 16), (0, 0, 3), (1, 5, 5)]
+    res = gpu_ctx.count_batch([hs[gi] for gi, _, _ in jobs], [p for _, p, _ in jobs], [q for _, _, q in jobs])
+    for (gi, p, q), r in zip(jobs, res):
+        if p == 0:
+            assert isinstance(r, gbc.GbcError) and r.status == gbc.GBC_ERR_ARG
+        elif gi == 5:
+            assert isinstance(r, gbc.GbcError) and r.status == gbc.GBC_ERR_OVERFLOW
+        else:
+            assert r == hs[gi].count(p, q), (gi, p, q)
+            if gi in (0, 3) or (gi == 1 and p + q <= 7):
+                assert r == oracle.count(graphs[gi], p, q), (gi, p, q)
+    # a second batch in a row gives the same numbers
+    res2 = gpu_ctx.count_batch([hs[gi] for gi, _, _ in jobs], [p for _, p, _ in jobs], [q for _, _, q in jobs])
+    assert [x if isinstance(x, int) else x.status for x in res] == [x if isinstance(x, int) else x.status for x in res2]
+    for h in hs:
+        h.close()
