@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch"],
+                    help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain")
     return ap.parse_args()
 
 
@@ -182,6 +184,9 @@ def main():
         if rank != 0:
             return
         reference_arm(args, pqs)
+        return
+    if args.workload == "batch":
+        batch_workload(args, rank, world, local)
         return
 
     import torch
@@ -316,6 +321,103 @@ def main():
             "gpu_launches": launches,
         }
         print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("256 chung-lu graphs, seeds 100..355: |E| = 10^U[3,6], |U|:|V| ratio U[0.25,4], "
+                  "exponent U[1.9,2.6] on both sides, (p,q) uniform in {2..6}^2")
+
+
+def batch_workload(args, rank, world, local):
+    """Queries/s of one gbc_count_batch over the 256-graph batch against 256 plain
+    gbc_count calls on the same resident graphs (same anchors, same counts)."""
+    import torch
+    import paper_2403_07858_gb300 as gbc
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    gbc.build()
+    jobs = [bipgen.batch_job(s) for s in range(100, 356)]
+    ctx = gbc.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    hs = [ctx.load(g) for g, _, _ in jobs]
+    ps = [p for _, p, _ in jobs]
+    qs = [q for _, _, q in jobs]
+    ctx.autotune(hs, ps, qs, time_limit_ms=30_000)
+    ref = [h.count(p, q) for h, p, q in zip(hs, ps, qs)]
+    for _ in range(args.warmup):
+        assert ctx.count_batch(hs, ps, qs) == ref
+        assert [h.count(p, q) for h, p, q in zip(hs, ps, qs)] == ref
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(fn):
+        out = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+            assert res == ref
+            barrier()
+        return statistics.mean(out)
+
+    with ClockSampler(local) as clk:
+        t_batch = timed(lambda: ctx.count_batch(hs, ps, qs))
+        t_plain = timed(lambda: [h.count(p, q) for h, p, q in zip(hs, ps, qs)])
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([t_batch, t_plain], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_batch, t_plain = float(t[0]), float(t[1])
+    n_q = len(jobs) * world
+    e2e = None
+    if not args.no_e2e:
+        pinned = [[torch.from_numpy(x).pin_memory().numpy() for x in (g.off_u, g.adj_u, g.off_v, g.adj_v)]
+                  for g, _, _ in jobs]
+        h2d = sum(int(x.nbytes) for arrs in pinned for x in arrs)
+        tt = []
+        for _ in range(args.steps):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hh = [ctx.load_graph(g.n_u, g.n_v, *arrs) for (g, _, _), arrs in zip(jobs, pinned)]
+            res = ctx.count_batch(hh, ps, qs)
+            for x in hh:
+                x.close()
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+            assert res == ref
+        e2e = {"value": n_q / statistics.mean(tt), "unit": "queries/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 16 * len(jobs)}
+    if rank == 0:
+        out = {
+            "metric": "batched queries/s", "value": n_q / t_batch, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 bitmaps, u128 counts", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "queries_per_step": len(jobs),
+                       "l2": "512 MiB written between timed steps",
+                       "anchors": "autotuned (both sides timed once, faster kept)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "plain": {"value": n_q / t_plain, "unit": "queries/s", "ms_per_step": t_plain * 1e3,
+                      "how": "256 sequential gbc_count calls on the same resident graphs"},
+            "batched_over_plain": t_plain / t_batch,
+            "e2e": e2e, "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    for h in hs:
+        h.close()
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()

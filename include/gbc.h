@@ -208,6 +208,22 @@ gbc_status gbc_count_p2_noalloc(int32_t nU, int32_t nV, const int32_t *offU_d, c
 gbc_status gbc_count_batch(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const int *p, const int *q,
                            gbc_u128 *out, gbc_status *per_job);
 
+/*
+ * gbc_autotune -- for each job (graphs[i], p[i], q[i]) with p, q >= 2, count it
+ * from both anchor sides (each run bounded by time_limit_ms, the second also by
+ * 1.2x the first's time), check that both agree, and remember the faster side
+ * in the context.  Later gbc_count / gbc_count_batch calls on the same (graph,
+ * p, q) use it (an explicit anchor option still wins).  The layer choice is a
+ * cost question the paper leaves to its CPU predecessor (Sec. IV); this
+ * measures it instead.  Entries are dropped when their graph is freed.
+ * Errors: GBC_ERR_ARG, and the errors of gbc_count except GBC_ERR_TIMEOUT.
+ */
+gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const int *p, const int *q,
+                        int time_limit_ms);
+
+/* The anchor gbc_autotune chose for (g, p, q): GBC_ANCHOR_U, GBC_ANCHOR_V, or 0 if untuned. */
+int gbc_tuned_anchor(gbc_graph_t g, int p, int q);
+
 /* Human-readable text of a status, and the calling thread's last error. */
 const char *gbc_status_string(gbc_status s);
 const char *gbc_last_error(void);

@@ -116,6 +116,9 @@ SIGNATURES = {
     "gbc_count_batch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(U128),
                                        ctypes.POINTER(ctypes.c_int)]),
+    "gbc_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "gbc_tuned_anchor": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbc_last_error": (ctypes.c_char_p, []),
 }
@@ -212,6 +215,9 @@ class Graph:
                                            ctypes.byref(info)), "gbc_count_ex")
         return out.value(), info.as_dict()
 
+    def tuned_anchor(self, p: int, q: int) -> str | None:
+        return _ANCHOR_NAMES.get(load_library().gbc_tuned_anchor(self._h, p, q))
+
     def count_per_root(self, p: int, q: int, anchor: str) -> tuple[int, list[int]]:
         n_a = self.n_u if anchor == "U" else self.n_v
         per = (U128 * max(1, n_a))()
@@ -271,6 +277,14 @@ class Context:
             else:
                 res.append(GbcError(st[i], load_library().gbc_status_string(st[i]).decode()))
         return res
+
+    def autotune(self, graphs, ps, qs, time_limit_ms: int = 60_000) -> None:
+        """Time both anchors for each (graph, p, q) and keep the faster for later counts."""
+        n = len(graphs)
+        hs = (ctypes.c_void_p * max(1, n))(*[g._h.value for g in graphs])
+        pa = (ctypes.c_int * max(1, n))(*ps)
+        qa = (ctypes.c_int * max(1, n))(*qs)
+        _check(load_library().gbc_autotune(self._h, n, hs, pa, qa, time_limit_ms), "gbc_autotune")
 
     def load(self, g) -> Graph:
         """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""

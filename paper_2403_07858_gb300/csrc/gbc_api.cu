@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -37,12 +38,25 @@ void gbc::set_last_error(const char *msg) { snprintf(t_err, sizeof t_err, "%s", 
         }                                                                                     \
     } while (0)
 
+constexpr int kAuxStreams = 8;
+
+struct TuneKey {
+    const void *graph;
+    int p, q;
+    bool operator<(const TuneKey &o) const {
+        return graph != o.graph ? graph < o.graph : (p != o.p ? p < o.p : q < o.q);
+    }
+};
+
 struct gbc_ctx_s {
     int device = 0;
     size_t budget = 0;
     int n_sms = 0;
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux[kAuxStreams] = {};      // per-job launches of a batch overlap on these
+    cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
+    std::map<TuneKey, int> tuned_anchor;     // filled by gbc_autotune
     std::mutex mu;
     int live_graphs = 0;
 };
@@ -113,6 +127,11 @@ gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out) {
     c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.8 * (double)free_b);
     CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     c->stream = c->own;
+    for (int i = 0; i < kAuxStreams; ++i) {
+        CK(cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -133,6 +152,11 @@ void gbc_ctx_destroy(gbc_ctx_t ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < kAuxStreams; ++i) {
+        cudaStreamDestroy(ctx->aux[i]);
+        cudaEventDestroy(ctx->join_ev[i]);
+    }
+    cudaEventDestroy(ctx->fork_ev);
     cudaStreamDestroy(ctx->own);
     delete ctx;
 }
@@ -149,6 +173,8 @@ void gbc_free_graph(gbc_graph_t g) {
     {
         std::lock_guard<std::mutex> lk(g->ctx->mu);
         g->ctx->live_graphs -= 1;
+        for (auto it = g->ctx->tuned_anchor.begin(); it != g->ctx->tuned_anchor.end();)
+            it = it->first.graph == g ? g->ctx->tuned_anchor.erase(it) : std::next(it);
     }
     delete g;
 }
@@ -410,6 +436,26 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
         CK(cudaMemsetAsync(d_stats, 0, sizeof(SearchStats), st));
     }
     std::vector<Small> hs(n);
+    // Per-job launches of a batch go to the auxiliary streams so that the
+    // kernels of small jobs overlap; fork/join keep them ordered against the
+    // context's stream.  A single job stays on the context's stream.
+    const bool multi = n > 1;
+    auto fork = [&]() -> cudaError_t {
+        if (!multi) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+        for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->aux[i], ctx->fork_ev, 0);
+        return e;
+    };
+    auto join = [&]() -> cudaError_t {
+        if (!multi) return cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(ctx->join_ev[i], ctx->aux[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[i], 0);
+        }
+        return e;
+    };
+    auto sj = [&](int i) { return multi ? ctx->aux[i % kAuxStreams] : st; };
     tm.mark(0, st);
     // ---- phase 0: arguments; single-vertex sets finish here
     for (int i = 0; i < n; ++i) {
@@ -453,15 +499,19 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
         CK(sc.get(&J.a.omega, nA));
         CK(sc.get(&J.a.tier_list, 3 * nA));
         CK(sc.get(&J.a.cand_count, nA));
-        CK(launch_root_omega(J.a, st));
         any = true;
     }
+    CK(fork());
+    for (int i = 0; i < n; ++i)
+        if (active(jobs[i])) CK(launch_root_omega(jobs[i].a, sj(i)));
+    CK(join());
     if (any) {
         CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
     // ---- phase 2: candidates (pass A) and, for |L| >= 3, the per-root offsets
     any = false;
+    std::vector<int64_t *> scan_tmp(n, nullptr);
     for (int i = 0; i < n; ++i) {
         Job &J = jobs[i];
         if (!active(J)) continue;
@@ -479,21 +529,30 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
             const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
             CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
         }
-        CK(launch_candidates(a, false, h.tier_count, ctx->n_sms, st));
         if (a.k >= 3) {
             const int64_t nA = a.g.nA;
-            int64_t *cand_off, *r_off, *s_off, *tmp;
+            int64_t *cand_off, *r_off, *s_off;
             CK(sc.get(&cand_off, nA + 1));
             CK(sc.get(&r_off, nA + 1));
             CK(sc.get(&s_off, nA + 1));
-            CK(sc.get(&tmp, 3 * ((nA + 1) / 2048 + 2)));
+            CK(sc.get(&scan_tmp[i], 3 * ((nA + 1) / 2048 + 2)));
             a.cand_off = cand_off;
             a.r_off = r_off;
             a.s_off = s_off;
-            CK(launch_root_offsets(a, cand_off, r_off, s_off, tmp, d_small[i].totals, st));
             any = true;
         }
     }
+    CK(fork());
+    for (int i = 0; i < n; ++i) {
+        Job &J = jobs[i];
+        if (!active(J)) continue;
+        CountArgs &a = J.a;
+        CK(launch_candidates(a, false, hs[i].tier_count, ctx->n_sms, sj(i)));
+        if (a.k >= 3)
+            CK(launch_root_offsets(a, const_cast<int64_t *>(a.cand_off), const_cast<int64_t *>(a.r_off),
+                                   const_cast<int64_t *>(a.s_off), scan_tmp[i], d_small[i].totals, sj(i)));
+    }
+    CK(join());
     tm.mark(1, st);
     if (any) {
         CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
@@ -539,6 +598,20 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
         }
         std::vector<CountArgs> enum_jobs;
         int max_wr = 2, max_wl = 2, max_k = 4;
+        // live units of the wave's enumeration, shared by its counts
+        int64_t unit_cap = 0;
+        for (int i : wave)
+            if (jobs[i].a.k >= 4) unit_cap += jobs[i].a.n_cand;
+        int2 *units_all = nullptr, *units_sorted = nullptr;
+        uint8_t *units_bucket = nullptr;
+        int32_t *ucounters = nullptr;  // n_all, bucket_count[16], cursor[16]
+        if (unit_cap > 0) {
+            CK(wave_sc.get(&units_all, unit_cap));
+            CK(wave_sc.get(&units_sorted, unit_cap));
+            CK(wave_sc.get(&units_bucket, unit_cap));
+            CK(wave_sc.get(&ucounters, 33));
+            CK(cudaMemsetAsync(ucounters, 0, 33 * 4, st));
+        }
         for (int i : wave) {
             CountArgs &a = jobs[i].a;
             const Small &h = hs[i];
@@ -553,15 +626,20 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
             if (a.k >= 4) {
                 CK(wave_sc.get(&a.S, h.totals[2]));
                 CK(cudaMemsetAsync(a.S, 0, std::max<int64_t>(h.totals[2], 1) * 4, st));
-                CK(wave_sc.get(&a.units, a.n_cand));
+                a.units_all = units_all;
+                a.units_bucket = units_bucket;
+                a.n_units_all = ucounters;
+                a.bucket_count = ucounters + 1;
             }
-            CK(launch_candidates(a, true, h.tier_count, ctx->n_sms, st));
         }
+        CK(fork());
+        for (int i : wave) CK(launch_candidates(jobs[i].a, true, hs[i].tier_count, ctx->n_sms, sj(i)));
         tm.mark(1, st);
         for (int i : wave) {
             CountArgs &a = jobs[i].a;
             const Small &h = hs[i];
-            CK(launch_pairs(a, ctx->n_sms, st));
+            if (a.k >= 4) a.job_id = (int32_t)enum_jobs.size();
+            CK(launch_pairs(a, ctx->n_sms, sj(i)));
             if (a.k >= 4) {
                 enum_jobs.push_back(a);
                 max_wr = std::max(max_wr, (int)row_stride(a.g.maxdegA));
@@ -569,19 +647,20 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
                 max_k = std::max(max_k, a.k);
             }
         }
+        CK(join());
         tm.mark(2, st);
         if (!enum_jobs.empty()) {
             CountArgs *d_jobs = nullptr;
-            int64_t *d_prefix = nullptr;
             int32_t *d_queue = nullptr;
             CK(wave_sc.get(&d_jobs, enum_jobs.size()));
-            CK(wave_sc.get(&d_prefix, enum_jobs.size() + 1));
             CK(wave_sc.get(&d_queue, 1));
             CK(cudaMemsetAsync(d_queue, 0, 4, st));
             CK(cudaMemcpyAsync(d_jobs, enum_jobs.data(), sizeof(CountArgs) * enum_jobs.size(),
                                cudaMemcpyHostToDevice, st));
-            CK(launch_enumerate(d_jobs, (int)enum_jobs.size(), d_prefix, d_queue, want_stats,
-                                opt ? opt->enum_warps : 0, max_wr, max_wl, max_k, ctx->n_sms, st));
+            CK(launch_sort_units(units_all, units_bucket, ucounters, ucounters + 1, ucounters + 17, units_sorted,
+                                 unit_cap, st));
+            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, want_stats, opt ? opt->enum_warps : 0,
+                                max_wr, max_wl, max_k, ctx->n_sms, st));
             // the job table is read by the launch: keep the host copy alive until it has run
             CK(cudaStreamSynchronize(st));
         }
@@ -608,7 +687,9 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
 }
 
 static int resolve_anchor(const gbc_graph_s *g, int p, int q, int requested) {
-    return requested ? requested : pick_anchor(g, p, q);
+    if (requested) return requested;
+    auto it = g->ctx->tuned_anchor.find(TuneKey{g, p, q});
+    return it != g->ctx->tuned_anchor.end() ? it->second : pick_anchor(g, p, q);
 }
 
 static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_options *opt, gbc_u128 *out,
@@ -737,4 +818,51 @@ extern "C" gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor
     cudaFreeAsync(d, st);
     cudaStreamSynchronize(st);
     return s;
+}
+
+// The autotuner: for each job it times the count from both anchors (the second
+// bounded by the first's time) and keeps the faster one for later counts of the
+// same (graph, p, q) on this context, plain or batched.  Anchors are the
+// knob with the largest effect (5-10x for p = q >= 5 on power-law graphs);
+// the cost model of pick_anchor is the starting point.
+extern "C" gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const int *p, const int *q,
+                                   int time_limit_ms) {
+    if (!ctx || n < 0 || (n > 0 && (!graphs || !p || !q))) return fail(GBC_ERR_ARG, "gbc_autotune: null argument");
+    for (int i = 0; i < n; ++i) {
+        if (!graphs[i] || graphs[i]->ctx != ctx || p[i] < 2 || q[i] < 2 || p[i] > GBC_MAX_PQ || q[i] > GBC_MAX_PQ)
+            continue;  // one-sided sets have no choice to tune
+        const TuneKey key{graphs[i], p[i], q[i]};
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            if (ctx->tuned_anchor.count(key)) continue;
+        }
+        const int first = pick_anchor(graphs[i], p[i], q[i]);
+        const int second = first == GBC_ANCHOR_U ? GBC_ANCHOR_V : GBC_ANCHOR_U;
+        gbc_count_options o;
+        memset(&o, 0, sizeof o);
+        o.anchor = first;
+        o.time_limit_ms = time_limit_ms;
+        gbc_count_info info;
+        gbc_u128 v1, v2;
+        gbc_status s1 = count_impl(graphs[i], p[i], q[i], &o, &v1, &info, 0, nullptr);
+        if (s1 != GBC_OK && s1 != GBC_ERR_TIMEOUT) return s1;
+        const float t1 = s1 == GBC_OK ? info.ms_total : 1e30f;
+        o.anchor = second;
+        o.time_limit_ms = s1 == GBC_OK ? std::max(1, (int)(t1 * 1.2f) + 1) : time_limit_ms;
+        gbc_status s2 = count_impl(graphs[i], p[i], q[i], &o, &v2, &info, 0, nullptr);
+        if (s2 != GBC_OK && s2 != GBC_ERR_TIMEOUT) return s2;
+        const float t2 = s2 == GBC_OK ? info.ms_total : 1e30f;
+        if (s1 == GBC_OK && s2 == GBC_OK && (v1.lo != v2.lo || v1.hi != v2.hi))
+            return fail(GBC_ERR_CUDA, "gbc_autotune: the two anchors disagree on (%d,%d)", p[i], q[i]);
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->tuned_anchor[key] = t2 < t1 ? second : first;
+    }
+    return GBC_OK;
+}
+
+extern "C" int gbc_tuned_anchor(gbc_graph_t g, int p, int q) {
+    if (!g) return 0;
+    std::lock_guard<std::mutex> lk(g->ctx->mu);
+    auto it = g->ctx->tuned_anchor.find(TuneKey{g, p, q});
+    return it == g->ctx->tuned_anchor.end() ? 0 : it->second;
 }

@@ -177,8 +177,13 @@ struct CountArgs {
     uint32_t *R;             // R rows: row j of root r is W_R(r) words at R + r_off[r] + j*W_R
     uint32_t *S;             // S rows: row j of root r is W_L(r) words at S + s_off[r] + j*W_L
     int64_t n_cand;          // sum c
-    int32_t *units;          // live level-2 units (global candidate index)
-    int32_t *n_units;        // [1]
+    int32_t *n_units;        // [1] live level-2 units of this count
+    // live units of every count in the enumeration launch, tagged for ordering
+    int32_t job_id;          // this count's index in the launch's job table
+    int2 *units_all;         // (job, global candidate index) of each live unit
+    uint8_t *units_bucket;   // floor(log2(children)) of each live unit, capped at 15
+    int32_t *n_units_all;    // [1]
+    int32_t *bucket_count;   // [16]
     int32_t *cand_max;       // [1] largest |C_L| of a kept root
     // global-tier hash slabs
     int32_t *slab;           // per-CTA slabs for roots with large omega
@@ -249,10 +254,16 @@ cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tie
 cudaError_t launch_root_offsets(const CountArgs &a, int64_t *cand_off, int64_t *r_off, int64_t *s_off,
                                 int64_t *tmp, int64_t *totals, cudaStream_t st);
 cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st);
-// One persistent launch over the level-2 units of n_jobs counts (d_jobs: a
-// device array of their CountArgs).  d_prefix: n_jobs + 1 int64 of scratch;
+// Orders the live units of a launch by their bucket, largest first, into
+// sorted (capacity entries); cursor: 16 zeroed ints.
+cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, const int32_t *n_all,
+                              const int32_t *bucket_count, int32_t *cursor, int2 *sorted, int64_t capacity,
+                              cudaStream_t st);
+// One persistent launch over the sorted level-2 units of several counts
+// (d_jobs: a device array of their CountArgs, indexed by the units' job id).
 // d_queue: a zeroed int32 work counter.
-cudaError_t launch_enumerate(const CountArgs *d_jobs, int n_jobs, int64_t *d_prefix, int32_t *d_queue, bool stats,
-                             int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms, cudaStream_t st);
+cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
+                             bool stats, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             cudaStream_t st);
 
 }  // namespace gbc

@@ -637,8 +637,14 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
             }
         }
         if (a.k >= 4 && lane == 0 && passes >= a.k - 2) {
-            const int slot = atomicAdd(a.n_units, 1);
-            a.units[slot] = (int32_t)gidx;
+            // live unit: tag it with the size class of its subtree (its number of
+            // children) so the enumeration can start the largest subtrees first
+            atomicAdd(a.n_units, 1);
+            const int slot = atomicAdd(a.n_units_all, 1);
+            const int b = min(15, 31 - __clz(passes));
+            a.units_all[slot] = make_int2(a.job_id, (int)gidx);
+            a.units_bucket[slot] = (uint8_t)b;
+            atomicAdd(&a.bucket_count[b], 1);
         }
         if (a.per_root && a.k == 3) {
             row_acc = warp_sum_u128(row_acc, ovf);
@@ -768,7 +774,7 @@ constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never
 
 template <bool STATS>
 __global__ void __launch_bounds__(256)
-k_enumerate(const CountArgs *jobs, int n_jobs, const int64_t *prefix, int32_t *queue, EnumLayout lay,
+k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, int32_t *queue, EnumLayout lay,
             uint32_t *gstack) {
     extern __shared__ __align__(16) uint32_t smem_stack[];
     __shared__ ulonglong2 s_binom[kSmemBinom];
@@ -803,23 +809,18 @@ k_enumerate(const CountArgs *jobs, int n_jobs, const int64_t *prefix, int32_t *q
 
     bool ovf = false;
     unsigned long long st_evals[2] = {0, 0}, st_passed[2] = {0, 0}, st_wr = 0, st_wl = 0;
-    const int64_t total_units = prefix[n_jobs];
+    const int total_units = *n_units;
     while (true) {
-        int64_t guidx = 0;
+        int guidx = 0;
         if (lane == 0) guidx = atomicAdd(queue, 1);
-        guidx = __shfl_sync(kFull, (long long)guidx, 0);
+        guidx = __shfl_sync(kFull, guidx, 0);
         if (guidx >= total_units || past_deadline(a0)) break;
-        // the job of this unit: the last job whose first unit is at or before it
-        int lo_j = 0, hi_j = n_jobs - 1;
-        while (lo_j < hi_j) {
-            const int mid = (lo_j + hi_j + 1) >> 1;
-            if (prefix[mid] <= guidx) lo_j = mid; else hi_j = mid - 1;
-        }
-        const CountArgs &a = jobs[lo_j];
+        const int2 unit = units[guidx];  // (job, global candidate index), largest subtrees first
+        const CountArgs &a = jobs[unit.x];
         const int k = a.k, kq = a.kq;
         const bool smem_binom = kq == kq0;
         unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
-        const int64_t gidx = a.units[guidx - prefix[lo_j]];
+        const int64_t gidx = unit.y;
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
         const int64_t c = a.cand_count[r];
@@ -1051,21 +1052,36 @@ k_enumerate(const CountArgs *jobs, int n_jobs, const int64_t *prefix, int32_t *q
     }
 }
 
-__global__ void k_unit_prefix(const CountArgs *jobs, int n_jobs, int64_t *prefix) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int64_t t = 0;
-        for (int i = 0; i < n_jobs; ++i) {
-            prefix[i] = t;
-            t += *jobs[i].n_units;
+__global__ void k_sort_units(const int2 *units_all, const uint8_t *bucket, const int32_t *n_all,
+                             const int32_t *bucket_count, int32_t *cursor, int2 *sorted) {
+    __shared__ int32_t base[16];
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int b = 15; b >= 0; --b) {  // the largest size class first
+            base[b] = t;
+            t += bucket_count[b];
         }
-        prefix[n_jobs] = t;
+    }
+    __syncthreads();
+    const int n = *n_all;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = bucket[i];
+        sorted[base[b] + atomicAdd(&cursor[b], 1)] = units_all[i];
     }
 }
 
-cudaError_t launch_enumerate(const CountArgs *d_jobs, int n_jobs, int64_t *d_prefix, int32_t *d_queue, bool stats,
-                             int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms, cudaStream_t st) {
-    k_unit_prefix<<<1, 32, 0, st>>>(d_jobs, n_jobs, d_prefix);
+cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, const int32_t *n_all,
+                              const int32_t *bucket_count, int32_t *cursor, int2 *sorted, int64_t capacity,
+                              cudaStream_t st) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((capacity + 255) / 256, 4096));
+    k_sort_units<<<grid, 256, 0, st>>>(units_all, bucket, n_all, bucket_count, cursor, sorted);
     ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
+                             bool stats, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             cudaStream_t st) {
     EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3)};
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;
@@ -1082,13 +1098,13 @@ cudaError_t launch_enumerate(const CountArgs *d_jobs, int n_jobs, int64_t *d_pre
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps_per_cta, smem);
         if (n_warps_hint <= 0) grid = n_sms * std::max(1, per_sm);
-        kern<<<grid, 32 * warps_per_cta, smem, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, nullptr);
+        kern<<<grid, 32 * warps_per_cta, smem, st>>>(d_jobs, units, n_units, d_queue, lay, nullptr);
         ++t_launches;
     } else {
         err = cudaMallocAsync(reinterpret_cast<void **>(&gstack), per_warp * warps_per_cta * grid, st);
         if (err != cudaSuccess) return err;
-        if (stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, gstack);
-        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, n_jobs, d_prefix, d_queue, lay, gstack);
+        if (stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, units, n_units, d_queue, lay, gstack);
+        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, units, n_units, d_queue, lay, gstack);
         ++t_launches;
         err = cudaGetLastError();
         cudaFreeAsync(gstack, st);

@@ -266,3 +266,18 @@ def test_batch_equals_single_counts(gpu_ctx):
     assert [x if isinstance(x, int) else x.status for x in res] == [x if isinstance(x, int) else x.status for x in res2]
     for h in hs:
         h.close()
+
+
+def test_autotune_keeps_counts_and_records_a_side(gpu_ctx):
+    g = bipgen.workload_small()
+    h = gpu_ctx.load(g)
+    pqs = [(2, 2), (3, 3), (4, 4), (2, 5), (5, 5)]
+    before = [h.count(p, q) for p, q in pqs]
+    gpu_ctx.autotune([h] * len(pqs), [p for p, _ in pqs], [q for _, q in pqs], time_limit_ms=20_000)
+    for (p, q), b in zip(pqs, before):
+        assert h.tuned_anchor(p, q) in ("U", "V")
+        assert h.count(p, q) == b
+    assert h.tuned_anchor(1, 3) is None
+    res = gpu_ctx.count_batch([h] * len(pqs), [p for p, _ in pqs], [q for _, q in pqs])
+    assert res == before
+    h.close()
