@@ -224,6 +224,38 @@ gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const i
 /* The anchor gbc_autotune chose for (g, p, q): GBC_ANCHOR_U, GBC_ANCHOR_V, or 0 if untuned. */
 int gbc_tuned_anchor(gbc_graph_t g, int p, int q);
 
+/*
+ * Serving (continuous batching).  gbc_serve_start starts `workers` threads
+ * (0 = 2), each with its own CUDA streams and an equal share of the context's
+ * scratch budget.  A free worker takes every waiting request, up to max_batch
+ * (0 = 256), and runs them as one batched pipeline (gbc_count_batch's); requests
+ * that arrive meanwhile wait for the next free worker, so successive batches
+ * overlap on the device.  max_queue (0 = 4096) bounds the waiting requests;
+ * time_limit_ms > 0 gives every request a device deadline (its poll then
+ * returns GBC_ERR_TIMEOUT).  The paper has no serving layer; each served count
+ * is the count of gbc_count.
+ */
+gbc_status gbc_serve_start(gbc_ctx_t ctx, int workers, int max_batch, int max_queue, int time_limit_ms);
+
+/* Stop serving: waiting requests are still run; results not yet polled are dropped. */
+gbc_status gbc_serve_stop(gbc_ctx_t ctx);
+
+/*
+ * gbc_submit -- queue the count of (g, p, q) and return its ticket at once
+ * (host output).  Starts the server with defaults if needed.  g must stay
+ * loaded until the request is polled.  Errors: GBC_ERR_ARG, GBC_ERR_REJECTED
+ * (max_queue requests already waiting).
+ */
+gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uint64_t *ticket);
+
+/*
+ * gbc_poll -- the result of a ticket: waits up to timeout_ms (0 = do not wait,
+ * < 0 = wait until done).  Returns GBC_PENDING if not finished; otherwise the
+ * request's status (its count in *out when GBC_OK), after which the ticket is
+ * retired.  Errors: GBC_ERR_ARG (unknown ticket, not serving) and the count's.
+ */
+gbc_status gbc_poll(gbc_ctx_t ctx, uint64_t ticket, int timeout_ms, gbc_u128 *out);
+
 /* Human-readable text of a status, and the calling thread's last error. */
 const char *gbc_status_string(gbc_status s);
 const char *gbc_last_error(void);

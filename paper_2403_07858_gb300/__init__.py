@@ -119,6 +119,10 @@ SIGNATURES = {
     "gbc_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "gbc_tuned_anchor": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "gbc_serve_start": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gbc_serve_stop": (ctypes.c_int, [_vp]),
+    "gbc_submit": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    "gbc_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U128)]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbc_last_error": (ctypes.c_char_p, []),
 }
@@ -285,6 +289,28 @@ class Context:
         pa = (ctypes.c_int * max(1, n))(*ps)
         qa = (ctypes.c_int * max(1, n))(*qs)
         _check(load_library().gbc_autotune(self._h, n, hs, pa, qa, time_limit_ms), "gbc_autotune")
+
+    # ---- serving
+    def serve_start(self, workers: int = 0, max_batch: int = 0, max_queue: int = 0, time_limit_ms: int = 0):
+        _check(load_library().gbc_serve_start(self._h, workers, max_batch, max_queue, time_limit_ms),
+               "gbc_serve_start")
+
+    def serve_stop(self):
+        _check(load_library().gbc_serve_stop(self._h), "gbc_serve_stop")
+
+    def submit(self, graph: "Graph", p: int, q: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load_library().gbc_submit(self._h, graph._h, p, q, ctypes.byref(t)), "gbc_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """The count of a ticket, or None while it is pending (timeout reached)."""
+        out = U128()
+        s = load_library().gbc_poll(self._h, ticket, timeout_ms, ctypes.byref(out))
+        if s == GBC_PENDING:
+            return None
+        _check(s, "gbc_poll")
+        return out.value()
 
     def load(self, g) -> Graph:
         """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""

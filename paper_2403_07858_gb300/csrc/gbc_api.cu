@@ -6,8 +6,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "gbc.h"
@@ -48,17 +53,42 @@ struct TuneKey {
     }
 };
 
+// A stream with its auxiliary streams: the counts of one pipeline run on it.
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaStream_t aux[kAuxStreams] = {};      // per-job launches of a batch overlap on these
+    cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
+    cudaError_t create(cudaStream_t main) {
+        st = main;
+        cudaError_t e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+        for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&aux[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_ev[i], cudaEventDisableTiming);
+        }
+        return e;
+    }
+    void destroy() {
+        for (int i = 0; i < kAuxStreams; ++i) {
+            if (aux[i]) cudaStreamDestroy(aux[i]);
+            if (join_ev[i]) cudaEventDestroy(join_ev[i]);
+        }
+        if (fork_ev) cudaEventDestroy(fork_ev);
+    }
+};
+
+struct Server;
+
 struct gbc_ctx_s {
     int device = 0;
     size_t budget = 0;
     int n_sms = 0;
     cudaStream_t own = nullptr;
-    cudaStream_t stream = nullptr;
-    cudaStream_t aux[kAuxStreams] = {};      // per-job launches of a batch overlap on these
-    cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
+    Lane lane;                               // the lane of the synchronous calls
+    std::mutex tune_mu;
     std::map<TuneKey, int> tuned_anchor;     // filled by gbc_autotune
     std::mutex mu;
     int live_graphs = 0;
+    Server *server = nullptr;                // gbc_submit / gbc_poll
 };
 
 struct gbc_graph_s {
@@ -94,6 +124,8 @@ struct Scratch {
     }
 };
 
+static void stop_server(gbc_ctx_s *ctx);
+
 extern "C" {
 
 const char *gbc_status_string(gbc_status s) {
@@ -126,12 +158,7 @@ gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out) {
     CK(cudaMemGetInfo(&free_b, &total_b));
     c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.8 * (double)free_b);
     CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
-    c->stream = c->own;
-    for (int i = 0; i < kAuxStreams; ++i) {
-        CK(cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming));
-    }
-    CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    CK(c->lane.create(c->own));
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
@@ -144,19 +171,16 @@ gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out) {
 gbc_status gbc_ctx_set_stream(gbc_ctx_t ctx, void *stream) {
     if (!ctx) return fail(GBC_ERR_ARG, "gbc_ctx_set_stream: null context");
     std::lock_guard<std::mutex> lk(ctx->mu);
-    ctx->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->own;
+    ctx->lane.st = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->own;
     return GBC_OK;
 }
 
 void gbc_ctx_destroy(gbc_ctx_t ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
-    for (int i = 0; i < kAuxStreams; ++i) {
-        cudaStreamDestroy(ctx->aux[i]);
-        cudaEventDestroy(ctx->join_ev[i]);
-    }
-    cudaEventDestroy(ctx->fork_ev);
+    stop_server(ctx);
+    cudaStreamSynchronize(ctx->lane.st);
+    ctx->lane.destroy();
     cudaStreamDestroy(ctx->own);
     delete ctx;
 }
@@ -164,7 +188,7 @@ void gbc_ctx_destroy(gbc_ctx_t ctx) {
 void gbc_free_graph(gbc_graph_t g) {
     if (!g) return;
     cudaSetDevice(g->ctx->device);
-    cudaStream_t st = g->ctx->stream;
+    cudaStream_t st = g->ctx->lane.st;
     void *ps[] = {g->offU, g->adjU, g->offV, g->adjV, g->degU, g->degV, g->adjV_byU,
                   g->mirrorU, g->adjU_byV, g->mirrorV, g->binom, g->n_ovf};
     for (void *p : ps)
@@ -173,6 +197,9 @@ void gbc_free_graph(gbc_graph_t g) {
     {
         std::lock_guard<std::mutex> lk(g->ctx->mu);
         g->ctx->live_graphs -= 1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
         for (auto it = g->ctx->tuned_anchor.begin(); it != g->ctx->tuned_anchor.end();)
             it = it->first.graph == g ? g->ctx->tuned_anchor.erase(it) : std::next(it);
     }
@@ -201,7 +228,7 @@ static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32
     if (nU < 0 || nV < 0) return fail(GBC_ERR_ARG, "gbc_load_graph: negative vertex count");
     std::lock_guard<std::mutex> lk(ctx->mu);
     CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = ctx->lane.st;
     // |E| from the ends of the two offset arrays
     int32_t eU = 0, eV = 0;
     if (host) {
@@ -401,6 +428,7 @@ struct Small {
 struct Job {
     gbc_graph_s *g = nullptr;
     int p = 0, q = 0, anchor = 0;
+    int time_limit_ms = 0;  // > 0: this job's own device deadline
     unsigned long long *per_root = nullptr;
     CountArgs a;
     Small h;
@@ -422,9 +450,9 @@ struct Job {
 // all jobs with |L| >= 4 is one persistent launch (a job table on the device).
 // Per-job scratch is granted in waves that fit the context's budget.
 // Returns a batch-level error (CUDA failure); per-job outcomes are in job.st.
-static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_count_options *opt, bool want_stats,
-                           Timer &tm, SearchStats *hs_out) {
-    cudaStream_t st = ctx->stream;
+static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vector<Job> &jobs,
+                           const gbc_count_options *opt, bool want_stats, Timer &tm, SearchStats *hs_out) {
+    cudaStream_t st = lane.st;
     const int n = (int)jobs.size();
     Scratch sc(st);
     Small *d_small = nullptr;
@@ -442,20 +470,20 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
     const bool multi = n > 1;
     auto fork = [&]() -> cudaError_t {
         if (!multi) return cudaSuccess;
-        cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
-        for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(ctx->aux[i], ctx->fork_ev, 0);
+        cudaError_t e = cudaEventRecord(lane.fork_ev, st);
+        for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(lane.aux[i], lane.fork_ev, 0);
         return e;
     };
     auto join = [&]() -> cudaError_t {
         if (!multi) return cudaSuccess;
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) {
-            e = cudaEventRecord(ctx->join_ev[i], ctx->aux[i]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[i], 0);
+            e = cudaEventRecord(lane.join_ev[i], lane.aux[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lane.join_ev[i], 0);
         }
         return e;
     };
-    auto sj = [&](int i) { return multi ? ctx->aux[i % kAuxStreams] : st; };
+    auto sj = [&](int i) { return multi ? lane.aux[i % kAuxStreams] : st; };
     tm.mark(0, st);
     // ---- phase 0: arguments; single-vertex sets finish here
     for (int i = 0; i < n; ++i) {
@@ -481,15 +509,17 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
         a.queues = s->queues;
         a.n_units = &s->n_units;
         a.cand_max = &s->cand_max;
-        a.deadline = &d_small[0].deadline;  // one deadline for the batch
+        a.deadline = &s->deadline;
         a.enum_words = &s->enum_words;
         a.stats = d_stats;
         a.per_root = J.per_root;
         J.trivial = (a.k > a.g.nA) || (a.kq > a.g.maxdegA) || a.g.nA == 0;
         if (!J.trivial && a.k == 1) CK(launch_single_vertex_sets(a, st));
     }
-    if (opt && opt->time_limit_ms > 0)
-        CK(launch_set_deadline(&d_small[0].deadline, (unsigned long long)opt->time_limit_ms * 1000000ull, st));
+    for (int i = 0; i < n; ++i) {
+        const int lim = jobs[i].time_limit_ms > 0 ? jobs[i].time_limit_ms : (opt ? opt->time_limit_ms : 0);
+        if (lim > 0) CK(launch_set_deadline(&d_small[i].deadline, (unsigned long long)lim * 1000000ull, st));
+    }
     auto active = [&](const Job &J) { return J.st == GBC_OK && !J.trivial && J.a.k >= 2; };
     // ---- phase 1: oriented wedge counts and root tiers
     bool any = false;
@@ -585,10 +615,10 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
         for (; pos < todo.size(); ++pos) {
             const int i = todo[pos];
             const size_t need = need_of(i);
-            if (used + need > ctx->budget) {
+            if (used + need > budget) {
                 if (wave.empty()) {
                     jobs[i].set_error(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need,
-                                      ctx->budget);
+                                      budget);
                     continue;
                 }
                 break;
@@ -670,14 +700,12 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
     if (d_stats && hs_out) CK(cudaMemcpyAsync(hs_out, d_stats, sizeof(SearchStats), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
-    const uint32_t batch_status = hs[0].status;
     for (int i = 0; i < n; ++i) {
         Job &J = jobs[i];
         J.h = hs[i];
         if (J.st != GBC_OK) continue;
-        if ((J.h.status | batch_status) & kStTimeout)
-            J.set_error(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its %d ms time limit", J.p, J.q,
-                        opt ? opt->time_limit_ms : 0);
+        if (J.h.status & kStTimeout)
+            J.set_error(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its time limit", J.p, J.q);
         else if (J.h.status & kStOverflow)
             J.set_error(GBC_ERR_OVERFLOW, "gbc_count: (%d,%d) count exceeds 2^128-1", J.p, J.q);
         else if (J.h.status)
@@ -688,6 +716,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, std::vector<Job> &jobs, const gbc_cou
 
 static int resolve_anchor(const gbc_graph_s *g, int p, int q, int requested) {
     if (requested) return requested;
+    std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
     auto it = g->ctx->tuned_anchor.find(TuneKey{g, p, q});
     return it != g->ctx->tuned_anchor.end() ? it->second : pick_anchor(g, p, q);
 }
@@ -714,7 +743,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
     tm.init(info != nullptr);
     SearchStats hs;
     memset(&hs, 0, sizeof hs);
-    gbc_status s = run_jobs(ctx, jobs, opt, want_stats, tm, &hs);
+    gbc_status s = run_jobs(ctx, ctx->lane, ctx->budget, jobs, opt, want_stats, tm, &hs);
     if (s != GBC_OK) return s;
     Job &J = jobs[0];
     if (J.st != GBC_OK) return fail(J.st, "%s", J.err);
@@ -778,7 +807,7 @@ extern "C" gbc_status gbc_count_batch(gbc_ctx_t ctx, int n, const gbc_graph_t *g
     Timer tm;
     tm.init(false);
     if (!jobs.empty()) {
-        gbc_status s = run_jobs(ctx, jobs, nullptr, false, tm, nullptr);
+        gbc_status s = run_jobs(ctx, ctx->lane, ctx->budget, jobs, nullptr, false, tm, nullptr);
         if (s != GBC_OK) return s;
     }
     for (size_t j = 0; j < jobs.size(); ++j) {
@@ -804,7 +833,7 @@ extern "C" gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor
     if (!g || !per_root || !total) return fail(GBC_ERR_ARG, "gbc_count_per_root: null argument");
     if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_count_per_root: anchor must be U or V");
     const int64_t nA = anchor == GBC_ANCHOR_U ? g->nU : g->nV;
-    cudaStream_t st = g->ctx->stream;
+    cudaStream_t st = g->ctx->lane.st;
     CK(cudaSetDevice(g->ctx->device));
     unsigned long long *d = nullptr;
     CK(cudaMallocAsync((void **)&d, (size_t)std::max<int64_t>(nA, 1) * 16, st));
@@ -833,7 +862,7 @@ extern "C" gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *grap
             continue;  // one-sided sets have no choice to tune
         const TuneKey key{graphs[i], p[i], q[i]};
         {
-            std::lock_guard<std::mutex> lk(ctx->mu);
+            std::lock_guard<std::mutex> lk(ctx->tune_mu);
             if (ctx->tuned_anchor.count(key)) continue;
         }
         const int first = pick_anchor(graphs[i], p[i], q[i]);
@@ -854,7 +883,7 @@ extern "C" gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *grap
         const float t2 = s2 == GBC_OK ? info.ms_total : 1e30f;
         if (s1 == GBC_OK && s2 == GBC_OK && (v1.lo != v2.lo || v1.hi != v2.hi))
             return fail(GBC_ERR_CUDA, "gbc_autotune: the two anchors disagree on (%d,%d)", p[i], q[i]);
-        std::lock_guard<std::mutex> lk(ctx->mu);
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
         ctx->tuned_anchor[key] = t2 < t1 ? second : first;
     }
     return GBC_OK;
@@ -862,7 +891,181 @@ extern "C" gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *grap
 
 extern "C" int gbc_tuned_anchor(gbc_graph_t g, int p, int q) {
     if (!g) return 0;
-    std::lock_guard<std::mutex> lk(g->ctx->mu);
+    std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
     auto it = g->ctx->tuned_anchor.find(TuneKey{g, p, q});
     return it == g->ctx->tuned_anchor.end() ? 0 : it->second;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: gbc_submit / gbc_poll.  Worker threads, each with its own lane of
+// streams and an equal share of the context's scratch budget, take every
+// request waiting when they become free (up to max_batch) and run them as one
+// batched pipeline.  Requests that arrive while batches are on the GPU wait for
+// the next free worker, so with several workers the pipelines of successive
+// batches overlap on the device (continuous batching).  Admission refuses a
+// request when max_queue requests are already waiting.
+struct Request {
+    uint64_t ticket = 0;
+    gbc_graph_s *g = nullptr;
+    int p = 0, q = 0, time_limit_ms = 0;
+    bool done = false;
+    gbc_status st = GBC_OK;
+    gbc_u128 val{0, 0};
+    char err[256] = "";
+};
+
+struct Server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> pending;
+    std::unordered_map<uint64_t, Request *> all;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    int max_batch = 256, max_queue = 4096, time_limit_ms = 0;
+    size_t budget_per_worker = 0;
+    std::vector<std::thread> threads;
+    std::vector<Lane> lanes;
+    std::vector<cudaStream_t> own_streams;
+};
+
+static void serve_loop(gbc_ctx_s *ctx, Server *sv, int w) {
+    cudaSetDevice(ctx->device);
+    while (true) {
+        std::vector<Request *> batch;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
+            if (sv->pending.empty()) return;  // stopping and drained
+            while (!sv->pending.empty() && (int)batch.size() < sv->max_batch) {
+                batch.push_back(sv->pending.front());
+                sv->pending.pop_front();
+            }
+        }
+        std::vector<Job> jobs(batch.size());
+        for (size_t i = 0; i < batch.size(); ++i) {
+            jobs[i].g = batch[i]->g;
+            jobs[i].p = batch[i]->p;
+            jobs[i].q = batch[i]->q;
+            jobs[i].time_limit_ms = batch[i]->time_limit_ms;
+            jobs[i].anchor = resolve_anchor(batch[i]->g, batch[i]->p, batch[i]->q, 0);
+        }
+        Timer tm;
+        tm.init(false);
+        const gbc_status s = run_jobs(ctx, sv->lanes[w], sv->budget_per_worker, jobs, nullptr, false, tm, nullptr);
+        const char *batch_err = s == GBC_OK ? "" : gbc_last_error();
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (size_t i = 0; i < batch.size(); ++i) {
+            Request *r = batch[i];
+            if (s != GBC_OK) {
+                r->st = s;
+                snprintf(r->err, sizeof r->err, "%s", batch_err);
+            } else {
+                r->st = jobs[i].st;
+                snprintf(r->err, sizeof r->err, "%s", jobs[i].err);
+                if (jobs[i].st == GBC_OK) r->val = gbc_u128{jobs[i].h.acc[0], jobs[i].h.acc[1]};
+            }
+            r->done = true;
+        }
+        sv->cv_done.notify_all();
+    }
+}
+
+static void stop_server(gbc_ctx_s *ctx) {
+    Server *sv = ctx->server;
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto &t : sv->threads) t.join();
+    for (auto &l : sv->lanes) l.destroy();
+    for (auto s : sv->own_streams) cudaStreamDestroy(s);
+    for (auto &kv : sv->all) delete kv.second;
+    delete sv;
+    ctx->server = nullptr;
+}
+
+extern "C" gbc_status gbc_serve_start(gbc_ctx_t ctx, int workers, int max_batch, int max_queue, int time_limit_ms) {
+    if (!ctx || workers < 0 || max_batch < 0 || max_queue < 0 || time_limit_ms < 0)
+        return fail(GBC_ERR_ARG, "gbc_serve_start: bad argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->server) return fail(GBC_ERR_ARG, "gbc_serve_start: already serving");
+    CK(cudaSetDevice(ctx->device));
+    Server *sv = new Server();
+    const int nw = workers ? workers : 2;
+    sv->max_batch = max_batch ? max_batch : 256;
+    sv->max_queue = max_queue ? max_queue : 4096;
+    sv->time_limit_ms = time_limit_ms;
+    sv->budget_per_worker = ctx->budget / (size_t)nw;
+    sv->lanes.resize(nw);
+    for (int w = 0; w < nw; ++w) {
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = sv->lanes[w].create(s);
+        if (e != cudaSuccess) {
+            for (auto &l : sv->lanes) l.destroy();
+            for (auto x : sv->own_streams) cudaStreamDestroy(x);
+            delete sv;
+            return fail(GBC_ERR_CUDA, "gbc_serve_start: %s", cudaGetErrorString(e));
+        }
+        sv->own_streams.push_back(s);
+    }
+    ctx->server = sv;
+    for (int w = 0; w < nw; ++w) sv->threads.emplace_back(serve_loop, ctx, sv, w);
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_serve_stop(gbc_ctx_t ctx) {
+    if (!ctx) return fail(GBC_ERR_ARG, "gbc_serve_stop: null context");
+    stop_server(ctx);
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uint64_t *ticket) {
+    if (!ctx || !g || !ticket || g->ctx != ctx) return fail(GBC_ERR_ARG, "gbc_submit: bad argument");
+    if (p < 1 || q < 1 || p > GBC_MAX_PQ || q > GBC_MAX_PQ)
+        return fail(GBC_ERR_ARG, "gbc_submit: p=%d q=%d outside [1, %d]", p, q, GBC_MAX_PQ);
+    if (!ctx->server) {
+        gbc_status s = gbc_serve_start(ctx, 0, 0, 0, 0);
+        if (s != GBC_OK && !ctx->server) return s;
+    }
+    Server *sv = ctx->server;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if ((int)sv->pending.size() >= sv->max_queue)
+        return fail(GBC_ERR_REJECTED, "gbc_submit: %d requests already waiting", (int)sv->pending.size());
+    Request *r = new Request();
+    r->ticket = sv->next_ticket++;
+    r->g = g;
+    r->p = p;
+    r->q = q;
+    r->time_limit_ms = sv->time_limit_ms;
+    sv->all[r->ticket] = r;
+    sv->pending.push_back(r);
+    *ticket = r->ticket;
+    sv->cv_work.notify_one();
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_poll(gbc_ctx_t ctx, uint64_t ticket, int timeout_ms, gbc_u128 *out) {
+    if (!ctx || !out) return fail(GBC_ERR_ARG, "gbc_poll: null argument");
+    Server *sv = ctx->server;
+    if (!sv) return fail(GBC_ERR_ARG, "gbc_poll: not serving");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return fail(GBC_ERR_ARG, "gbc_poll: unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (!r->done) {
+        if (timeout_ms > 0)
+            sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; });
+        else if (timeout_ms < 0)
+            sv->cv_done.wait(lk, [&] { return r->done; });
+        if (!r->done) return GBC_PENDING;
+    }
+    const gbc_status s = r->st;
+    if (s == GBC_OK) *out = r->val;
+    else fail(s, "%s", r->err);
+    sv->all.erase(it);
+    delete r;
+    return s;
 }

@@ -358,7 +358,7 @@ k_cand_warp(CountArgs a) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(queue, 1);
         idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= n || past_deadline(a)) break;
+        if (idx >= n || __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
         const int32_t u = a.tier_list[idx];
         if (BUILD && a.cand_count[u] < a.k - 1) continue;
         process_root<1, BUILD>(a, u, my_keys, my_vals, my_sort, s_int[w], acc, ovf);
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
         int64_t gidx = 0;
         if (lane == 0) gidx = atomicAdd(a.queues + 6, 1);
         gidx = __shfl_sync(kFull, gidx, 0);
-        if (gidx >= a.n_cand || past_deadline(a)) break;
+        if (gidx >= a.n_cand || __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
         const int64_t c = a.cand_count[r];
@@ -814,9 +814,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         int guidx = 0;
         if (lane == 0) guidx = atomicAdd(queue, 1);
         guidx = __shfl_sync(kFull, guidx, 0);
-        if (guidx >= total_units || past_deadline(a0)) break;
+        if (guidx >= total_units) break;
         const int2 unit = units[guidx];  // (job, global candidate index), largest subtrees first
         const CountArgs &a = jobs[unit.x];
+        if (__shfl_sync(kFull, (int)past_deadline(a), 0)) continue;  // this job ran out of time: drop its units
         const int k = a.k, kq = a.kq;
         const bool smem_binom = kq == kq0;
         unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
@@ -843,7 +844,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         int lv = 0;
         unsigned batches = 0;
         while (true) {
-            if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a0), 0)) break;
+            if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
             const uint32_t dm = dmask[lv];
             if (dm != 0) {
                 const int t = __ffs(dm) - 1;
