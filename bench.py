@@ -50,8 +50,12 @@ def _args():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch"],
-                    help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
+                    help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain; "
+                         "serve: Poisson query stream over 8 resident graphs")
+    ap.add_argument("--serve-scale", type=float, default=1.0, help="size factor of the serving graphs (1 = stated)")
+    ap.add_argument("--serve-limit-ms", type=int, default=30_000, help="per-request device deadline when serving")
+    ap.add_argument("--serve-per-rate", type=int, default=120, help="queries per arrival rate")
     return ap.parse_args()
 
 
@@ -187,6 +191,9 @@ def main():
         return
     if args.workload == "batch":
         batch_workload(args, rank, world, local)
+        return
+    if args.workload == "serve":
+        serve_workload(args, rank, world, local)
         return
 
     import torch
@@ -421,6 +428,92 @@ def batch_workload(args, rank, world, local):
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def serve_workload(args, rank, world, local):
+    """Poisson query streams at rising rates against the continuous-batching
+    server; latency = completion - arrival.  The single-stream service rate is
+    measured first with sequential plain counts of the same query stream."""
+    import concurrent.futures as cf
+    import numpy as np
+    import torch
+    import paper_2403_07858_gb300 as gbc
+    torch.cuda.set_device(local)
+    gbc.build()
+    t0 = time.perf_counter()
+    graphs = [bipgen.serving_graph(i, args.serve_scale) for i in range(8)]
+    t_gen = time.perf_counter() - t0
+    ctx = gbc.Context(local)
+    hs = [ctx.load(g) for g in graphs]
+    lim = args.serve_limit_ms
+    stream = bipgen.serving_queries(24 + 5 * args.serve_per_rate, seed=600)
+    # single stream: sequential plain counts of the first 24 queries
+    alone, serv_ms = {}, []
+    for (gi, p, q) in stream[:24]:
+        t = time.perf_counter()
+        try:
+            alone[(gi, p, q)] = hs[gi].count_ex(p, q, time_limit_ms=lim)[0]
+        except gbc.CountTimeout:
+            alone[(gi, p, q)] = "timeout"
+        serv_ms.append((time.perf_counter() - t) * 1e3)
+    mu = 1e3 / statistics.mean(serv_ms)  # queries/s of one stream
+    ctx.serve_start(workers=2, max_batch=64, max_queue=100_000, time_limit_ms=lim)
+    rng = np.random.default_rng(601)
+    rates, mismatches = [], 0
+    for ri, f in enumerate([0.25, 0.5, 1.0, 2.0, 4.0]):
+        lam = f * mu
+        qs = stream[:24] + stream[24 + ri * args.serve_per_rate: 24 + (ri + 1) * args.serve_per_rate]
+        qs = qs[:max(24, min(len(qs), int(lam * 120) + 24))]
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, len(qs)))
+        done_at, status = [None] * len(qs), [None] * len(qs)
+        pool = cf.ThreadPoolExecutor(max_workers=64)
+        start = time.perf_counter()
+        futs = []
+
+        def wait(i, ticket):
+            try:
+                v = ctx.poll(ticket, -1)
+                status[i] = v
+            except gbc.CountTimeout:
+                status[i] = "timeout"
+            except gbc.GbcError as e:
+                status[i] = f"error {e.status}"
+            done_at[i] = time.perf_counter() - start
+
+        for i, (gi, p, q) in enumerate(qs):
+            now = time.perf_counter() - start
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            futs.append(pool.submit(wait, i, ctx.submit(hs[gi], p, q)))
+        for fu in futs:
+            fu.result()
+        pool.shutdown()
+        lat = [done_at[i] - arrivals[i] for i in range(len(qs))]
+        for i, key in enumerate(qs[:24]):
+            if alone[key] != "timeout" and status[i] != alone[key]:
+                mismatches += 1
+        span = max(done_at) - arrivals[0]
+        rates.append({"offered_qps": lam, "factor": f, "queries": len(qs),
+                      "served_qps": len(qs) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                      "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                      "timeouts": sum(1 for x in status if x == "timeout")})
+    ctx.serve_stop()
+    best = max(r["served_qps"] for r in rates)
+    if rank == 0:
+        out = {"metric": "batched queries/s, p99 latency", "value": best, "unit": "queries/s",
+               "n_gpus": world, "steps": 5, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "u32 bitmaps, u128 counts", "data": "synthetic",
+               "config": {"workload": f"8 resident chung-lu graphs (exponent 2.1): seed 500 with "
+                                      f"{graphs[0].n_u}/{graphs[0].n_v}/{graphs[0].n_edges} vertices/edges, "
+                                      f"seeds 501..507 |E| log-uniform in [1e5,1e7] x {args.serve_scale}; "
+                                      "queries: graph uniform, p,q uniform in {2..8}, Poisson arrivals",
+                          "scale": args.serve_scale, "per_request_limit_ms": lim, "workers": 2,
+                          "graph_generation_s": t_gen},
+               "single_stream_qps": mu, "rates": rates, "served_equals_alone_mismatches": mismatches}
+        print(json.dumps(out), flush=True)
+    for h in hs:
+        h.close()
+    ctx.close()
 
 
 def _ncu_traffic():

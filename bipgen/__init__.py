@@ -320,3 +320,26 @@ def batch_job(seed: int) -> tuple[BipartiteGraph, int, int]:
     n_v = max(2, n_tot - n_u)
     n_edges = min(n_edges, n_u * n_v // 2)
     return chung_lu(seed, n_u, n_v, n_edges, gamma, gamma), p, q
+
+
+def serving_graph(i: int, scale: float = 1.0) -> BipartiteGraph:
+    """Graph i (0..7) of the serving set.  0: Chung-Lu seed 500, |U|=10M, |V|=5M,
+    |E|=100M, exponent 2.1; 1..7: seeds 501..507, |E| log-uniform in [1e5, 1e7],
+    |U|+|V| = ceil(|E|/5) split by a ratio U[0.25, 4], exponent 2.1.  ``scale``
+    multiplies every size (1.0 = the stated workload)."""
+    if i == 0:
+        return chung_lu(500, int(10_000_000 * scale), int(5_000_000 * scale), int(100_000_000 * scale), 2.1, 2.1)
+    seed = 500 + i
+    r = uniform(stream_state(seed, "SERVE"), 0, 2)
+    n_edges = int(round(10.0 ** (5.0 + 2.0 * float(r[0]))) * scale)
+    ratio = 0.25 + 3.75 * float(r[1])
+    n_tot = -(-n_edges // 5)
+    n_u = max(2, int(round(n_tot * ratio / (1.0 + ratio))))
+    n_v = max(2, n_tot - n_u)
+    return chung_lu(seed, n_u, n_v, min(n_edges, n_u * n_v // 2), 2.1, 2.1)
+
+
+def serving_queries(n: int, seed: int = 600) -> list[tuple[int, int, int]]:
+    """n queries (graph index 0..7, p, q) with p, q uniform in {2..8}."""
+    r = uniform(stream_state(seed, "QUERIES"), 0, 3 * n).reshape(n, 3)
+    return [(int(a * 8), 2 + int(b * 7), 2 + int(c * 7)) for a, b, c in r]
