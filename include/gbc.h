@@ -121,7 +121,12 @@ typedef struct {
     int32_t enum_warps;  /* warps of the persistent enumeration launch; 0 = auto */
     int32_t time_limit_ms; /* > 0: device-side deadline; past it the kernels stop and the
                               call returns GBC_ERR_TIMEOUT (the count is then not valid) */
-    int32_t reserved[4];
+    int32_t root_begin;  /* root_end > root_begin: only anchor vertices in [root_begin, root_end)
+                            root search trees, i.e. the count of the bicliques whose lowest-ranked
+                            anchor vertex lies there (Def. 2 reading); disjoint ranges that cover
+                            the anchor side add up to the count (the split used across GPUs) */
+    int32_t root_end;
+    int32_t reserved[2];
 } gbc_count_options;
 
 /* Facts about one count (host output of gbc_count_ex). */

@@ -59,7 +59,8 @@ class U128(ctypes.Structure):
 class CountOptions(ctypes.Structure):
     _fields_ = [("anchor", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("enum_warps", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("root_begin", ctypes.c_int32), ("root_end", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class CountInfo(ctypes.Structure):
@@ -208,12 +209,17 @@ class Graph:
         return out.value()
 
     def count_ex(self, p: int, q: int, anchor: str = "auto", stats: bool = False,
-                 enum_warps: int = 0, time_limit_ms: int = 0) -> tuple[int, dict]:
+                 enum_warps: int = 0, time_limit_ms: int = 0,
+                 roots: tuple[int, int] | None = None) -> tuple[int, dict]:
+        """roots: count only the search trees rooted in this half-open range of
+        anchor vertices (give the anchor explicitly when splitting a count)."""
         opt = CountOptions()
         opt.anchor = ANCHORS[anchor]
         opt.collect_stats = 1 if stats else 0
         opt.enum_warps = enum_warps
         opt.time_limit_ms = time_limit_ms
+        if roots is not None:
+            opt.root_begin, opt.root_end = int(roots[0]), int(roots[1])
         out, info = U128(), CountInfo()
         _check(load_library().gbc_count_ex(self._h, p, q, ctypes.byref(opt), ctypes.byref(out),
                                            ctypes.byref(info)), "gbc_count_ex")

@@ -501,6 +501,12 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             a.kq = J.p;
         }
         a.binom = BinomTable{g->binom, g->n_ovf, g->binom_nmax};
+        a.root_begin = 0;
+        a.root_end = a.g.nA;
+        if (opt && opt->root_end > opt->root_begin) {
+            a.root_begin = std::max(0, opt->root_begin);
+            a.root_end = std::min(a.g.nA, opt->root_end);
+        }
         Small *s = d_small + i;
         a.acc = s->acc;
         a.status = &s->status;

@@ -161,6 +161,7 @@ struct CountArgs {
     BinomTable binom;
     int k;          // |L| on the anchor side
     int kq;         // |R| on the other side
+    int32_t root_begin, root_end;  // roots taken: [root_begin, root_end)
     // root classification
     int32_t *omega;          // [nA] oriented wedge count of each root
     int32_t *tier_list;      // 3 lists of roots, each of capacity nA

@@ -25,7 +25,7 @@ __global__ void k_single_vertex_sets(CountArgs a) {
     const int64_t n = a.g.nA;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((n + 31) / 32) * 32;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < n) {
+        if (i < n && i >= a.root_begin && i < a.root_end) {
             bool o = false;
             ulonglong2 v = binom_lookup(a.binom, a.kq, a.g.degA[i], o);
             if (a.per_root) {
@@ -41,7 +41,8 @@ __global__ void k_single_vertex_sets(CountArgs a) {
         if (ovf) atomicOr(a.status, kStOverflow);
         atomic_add_u128(a.acc, acc, a.status);
     }
-    if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats->roots, (unsigned long long)n);
+    if (a.stats && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(&a.stats->roots, (unsigned long long)((n < a.root_end ? n : a.root_end) - max(0, a.root_begin)));
 }
 
 __global__ void k_set_deadline(unsigned long long *deadline, unsigned long long limit_ns) {
@@ -78,7 +79,8 @@ __global__ void k_root_omega(CountArgs a) {
             }
         }
         a.omega[u] = (int32_t)om;
-        if (om >= (int64_t)(a.k - 1) * a.kq && om > 0) {
+        const bool mine = u >= a.root_begin && u < a.root_end;
+        if (mine && om >= (int64_t)(a.k - 1) * a.kq && om > 0) {
             const int tier = om <= kWarpTierOmega ? 0 : (om <= kCtaTierOmega ? 1 : 2);
             const int slot = atomicAdd(&a.tier_count[tier], 1);
             a.tier_list[(int64_t)tier * g.nA + slot] = (int32_t)u;

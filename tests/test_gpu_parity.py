@@ -281,3 +281,20 @@ def test_autotune_keeps_counts_and_records_a_side(gpu_ctx):
     res = gpu_ctx.count_batch([h] * len(pqs), [p for p, _ in pqs], [q for _, q in pqs])
     assert res == before
     h.close()
+
+
+def test_root_ranges_add_up_to_the_count(gpu_ctx):
+    """Disjoint root ranges (the multi-GPU split) sum to the whole count, and
+    each range equals the oracle's count over the same roots."""
+    from paper_2403_07858_gb300.shard import root_ranges
+    g = bipgen.workload_small()
+    h = gpu_ctx.load(g)
+    for p, q, anchor in [(3, 3, "U"), (4, 4, "V"), (1, 3, "U"), (2, 2, "V")]:
+        n_a = g.n_u if anchor == "U" else g.n_v
+        deg = np.diff(g.off_u if anchor == "U" else g.off_v).astype(float)
+        parts = [h.count_ex(p, q, anchor=anchor, roots=r)[0] for r in root_ranges(deg ** 2, 3)]
+        assert sum(parts) == h.count(p, q)
+        r = root_ranges(deg ** 2, 3)[1]
+        assert parts[1] == oracle.count(g, p, q, anchor=anchor, roots=r)
+        assert h.count_ex(p, q, anchor=anchor, roots=(0, n_a))[0] == h.count(p, q)
+    h.close()
