@@ -228,12 +228,8 @@ def er_planted(seed: int, n_u: int, n_v: int, n_edges: int, n_planted: int,
         return lambda start, m: (splitmix64(st, start, m) % np.uint64(n)).astype(np.int64)
 
     us, vs = _distinct_pairs(seed, n_u, n_v, n_edges, draw(su, n_u), draw(sv, n_v))
-    sp = stream_state(seed, "PLANT")
     extra_u, extra_v = [], []
-    for b in range(n_planted):
-        base = 2 * b
-        lu = np.argsort(splitmix64(sp, base * max(n_u, n_v), n_u), kind="stable")[:k]
-        lv = np.argsort(splitmix64(sp, (base + 1) * max(n_u, n_v), n_v), kind="stable")[:k]
+    for lu, lv in planted_blocks(seed, n_u, n_v, n_planted, k):
         gu, gv = np.meshgrid(lu, lv, indexing="ij")
         extra_u.append(gu.ravel())
         extra_v.append(gv.ravel())
@@ -241,6 +237,18 @@ def er_planted(seed: int, n_u: int, n_v: int, n_edges: int, n_planted: int,
         us = np.concatenate([us] + extra_u)
         vs = np.concatenate([vs] + extra_v)
     return from_edges(n_u, n_v, us, vs)
+
+
+def planted_blocks(seed: int, n_u: int, n_v: int, n_planted: int, k: int):
+    """The vertex sets (U part, V part) of the blocks ``er_planted`` plants."""
+    sp = stream_state(seed, "PLANT")
+    out = []
+    for b in range(n_planted):
+        base = 2 * b
+        lu = np.argsort(splitmix64(sp, base * max(n_u, n_v), n_u), kind="stable")[:k]
+        lv = np.argsort(splitmix64(sp, (base + 1) * max(n_u, n_v), n_v), kind="stable")[:k]
+        out.append((lu, lv))
+    return out
 
 
 def tiny_random(seed: int, n_u: int, n_v: int, density: float) -> BipartiteGraph:
