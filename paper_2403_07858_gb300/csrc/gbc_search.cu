@@ -17,6 +17,12 @@ namespace gbc {
 
 thread_local int t_launches = 0;
 
+// For |L| >= 4 each root also keeps T: for each of its kTPos most shared
+// positions, the bitmap of the candidates containing it (the transpose of the
+// first two word pairs of R), placed after the root's S block.
+constexpr int kTPos = 128;
+
+
 // ---------------------------------------------------------------------------
 // k == 1: every anchor vertex alone is L; it contributes C(deg, kq).
 __global__ void k_single_vertex_sets(CountArgs a) {
@@ -328,6 +334,8 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
     // sit at pair pw * c + x, so the first pair of every row forms one
     // contiguous c * 8 B block (deep C_R spans rarely go past it).
     uint32_t *Rb = a.R + a.r_off[u];
+    const int32_t WLc = (c + 31) >> 5;
+    uint32_t *Tb = a.k >= 4 ? a.S + a.s_off[u] + (int64_t)c * WLc : nullptr;
     for_each_wedge<NW>(g, u, [&](int32_t w, int32_t i) {
         const int32_t slot = table_find(keys, log2slots, w, a.status);
         const int32_t v = slot >= 0 ? vvals[slot] : 0;
@@ -335,6 +343,7 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
             const int32_t np = __ldcg(&pm[i]);
             const int64_t x = -1 - v;
             atomicOr(&Rb[2 * ((int64_t)(np >> 6) * c + x) + ((np >> 5) & 1)], 1u << (np & 31));
+            if (Tb && np < kTPos) atomicOr(&Tb[(int64_t)np * WLc + (x >> 5)], 1u << (x & 31));
         }
     });
     G::sync();
@@ -462,7 +471,7 @@ __device__ __forceinline__ void root_sizes(const CountArgs &a, int64_t r, int64_
     if (cc < a.k - 1 || cc == 0) return;
     c = cc;
     wr = (int64_t)cc * row_stride(a.g.degA[r]);
-    wl = a.k >= 4 ? (int64_t)cc * ((cc + 31) >> 5) : 0;
+    wl = a.k >= 4 ? (int64_t)(cc + kTPos) * ((cc + 31) >> 5) : 0;
 }
 
 template <typename T>
@@ -833,6 +842,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         const int32_t WL = (int32_t)((c + 31) >> 5);
         const uint2 *Rp = reinterpret_cast<const uint2 *>(a.R + a.r_off[r]);
         const uint32_t *St = a.S + a.s_off[r];
+        const uint32_t *Tb = St + (int64_t)c * WL;  // T: candidates per shared position
         u128 unit_acc = 0;
         // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
         {
@@ -937,37 +947,64 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                         nl += __popc(nz);
                         if (nl > kLeafList - 32 || (w + 1 == WL && nl > 0)) {
                             __syncwarp();
-                            // Phase B over LM[0, nl)
+                            // Phase B over LM[0, nl): one staged word (parent y, word w,
+                            // leaves M) per lane.  The leaves' counts |C_R(y) & R_x|
+                            // for all x of the word are summed bit-sliced: for each
+                            // position i of C_R(y) the word T_i[w] of candidates
+                            // containing i is added into 4-bit vertical counters, and
+                            // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.
                             for (int e0 = 0; e0 < nl; e0 += 32) {
                                 const int e = e0 + lane;
-                                const uint32_t m = e < nl ? LM[e] : 0u;
-                                const uint32_t tg = e < nl ? LT[e] : 0u;
-                                const int cnt = __popc(m);
-                                const int incl = warp_incl_scan(cnt);
-                                const int total = __shfl_sync(kFull, incl, 31);
-                                for (int rb = 0; rb < total; rb += 32) {
-                                    const int rk = rb + lane;
-                                    int src = 0;
+                                if (e < nl) {
+                                    const uint32_t M = LM[e], tg = LT[e];
+                                    const int w = (int)(tg & 0xffffu);
+                                    const uint4 cy = CRY[tg >> 16];
+                                    const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
+                                    if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
+                                    if (m < 16) {
+                                        uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
 #pragma unroll
-                                    for (int b = 16; b >= 1; b >>= 1) {
-                                        const int v = __shfl_sync(kFull, incl, src + b - 1);
-                                        if (v <= rk) src += b;
-                                    }
-                                    src = min(src, 31);
-                                    const uint32_t ws = __shfl_sync(kFull, m, src);
-                                    const int ex = __shfl_sync(kFull, incl - cnt, src);
-                                    const uint32_t t = __shfl_sync(kFull, tg, src);
-                                    if (rk < total) {
-                                        const int32_t x = (int32_t)((t & 0xffffu) << 5) + select_bit(ws, rk - ex);
-                                        const uint4 cy = CRY[t >> 16];
-                                        int n = popc2(make_uint2(cy.x, cy.y), Rp[x]);
-                                        if (sp > 1) n += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
-                                        words += 2 * sp;
-                                        if (STATS) { st_evals[1] += 1; st_wr += WRm; }
-                                        if (n >= kq) {
-                                            if (STATS) st_passed[1] += 1;
-                                            if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
-                                            else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
+                                        for (int qw = 0; qw < 4; ++qw) {
+                                            uint32_t bits = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
+                                            while (bits) {
+                                                const int i = (qw << 5) + __ffs(bits) - 1;
+                                                bits &= bits - 1;
+                                                const uint32_t t = Tb[(int64_t)i * WL + w] & M;
+                                                const uint32_t c0 = b0 & t;
+                                                b0 ^= t;
+                                                const uint32_t c1 = b1 & c0;
+                                                b1 ^= c0;
+                                                const uint32_t c2 = b2 & c1;
+                                                b2 ^= c1;
+                                                b3 ^= c2;
+                                            }
+                                        }
+                                        words += m + 1;
+                                        for (int v = kq; v <= m; ++v) {
+                                            const uint32_t eq = M & ((v & 1) ? b0 : ~b0) & ((v & 2) ? b1 : ~b1) &
+                                                                ((v & 4) ? b2 : ~b2) & ((v & 8) ? b3 : ~b3);
+                                            const int cnt = __popc(eq);
+                                            if (cnt) {
+                                                if (STATS) st_passed[1] += cnt;
+                                                const ulonglong2 bc = (smem_binom && v < kSmemBinom)
+                                                                          ? s_binom[v] : binom_lookup(a.binom, kq, v, ovf);
+                                                add_u128(unit_acc, (u128)bc.x * (unsigned)cnt, ovf);
+                                            }
+                                        }
+                                    } else {
+                                        // a wide C_R(y): the leaves one by one
+                                        uint32_t bits = M;
+                                        while (bits) {
+                                            const int32_t x = (w << 5) + __ffs(bits) - 1;
+                                            bits &= bits - 1;
+                                            int n = popc2(make_uint2(cy.x, cy.y), Rp[x]);
+                                            if (sp > 1) n += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
+                                            words += 2 * sp;
+                                            if (n >= kq) {
+                                                if (STATS) st_passed[1] += 1;
+                                                if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                                                else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
+                                            }
                                         }
                                     }
                                 }
