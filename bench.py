@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-roofline", action="store_true",
+                    help="skip the untimed statistics pass and microbenchmarks behind the roofline")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
                     help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain; "
                          "serve: Poisson query stream over 8 resident graphs")
@@ -249,6 +251,16 @@ def main():
                     enum_words += info["enum_words"]
                     enum_launches += 1
     clocks = clk.summary()
+    # Algorithmic work of the enumeration launches (untimed): the model words
+    # of the search nodes the enumeration kernel evaluates, counted by the
+    # statistics pass of the same counts (equal to the oracle's instrumented
+    # traversal on the graphs the tests check).
+    model_words = {}
+    for k in ([] if args.no_roofline else pqs):
+        n, sinfo = h.count_ex(k, k, stats=True)
+        assert n == ref_counts[k]
+        if sinfo["words_enum"] > 0:
+            model_words[k] = sinfo["words_enum"]
     h.close()
     ms_step = statistics.mean(step_ms)
     if dist is not None:
@@ -287,24 +299,32 @@ def main():
 
     # ---- roofline of the dominant kernel (the enumeration).  ncu shows it bound
     # by instruction issue on the integer pipe with its bitmap rows resident in
-    # L1/L2 (DRAM traffic is a few hundred MB per launch against terabytes of
-    # words), so the roofline is ALU: each bitmap word the kernel loads costs one
-    # AND, one POPC and one ADD; the peak is 128 integer lanes per SM per clock.
+    # L1/L2, so the roofline is ALU.  Algorithmic work: per evaluated search node
+    # ceil(d/32) C_R words, plus ceil(c/32) C_L words for internal nodes, each
+    # word one AND and one POPC; peak: 128 integer lanes per SM per clock.
     peaks = _peaks()
     roof = None
-    if enum_launches:
+    if enum_launches and model_words:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_tops = n_sms * 128 * sm_max * 1e6 / 1e12
-        ops_per_launch = 3.0 * enum_words / enum_launches
+        words_per_launch = sum(model_words.values()) / len(model_words)
+        ops_per_launch = 2.0 * words_per_launch
         ms_per_launch = enum_ms / enum_launches
         achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e12
+        micro = gbc.measure_int_peaks(local)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": _ncu_traffic(), "kernel": "k_enumerate",
                 "peak_source": f"derived: {n_sms} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz max SM clock",
-                "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 3,
-                "words_per_launch": enum_words / enum_launches, "launches": enum_launches,
-                "ms_per_launch": ms_per_launch}
+                "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
+                "model_words_per_launch": words_per_launch,
+                "loaded_words_per_launch": enum_words / enum_launches,
+                "launches": enum_launches, "ms_per_launch": ms_per_launch,
+                "microbench": {
+                    "and_popc_add_loop_words_per_s": micro["and_popc_words_per_s"],
+                    "model_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
+                                                   / micro["and_popc_words_per_s"],
+                    "l2_and_popc_stream_gbs": micro["l2_bytes_per_s"] / 1e9}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

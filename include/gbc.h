@@ -149,6 +149,8 @@ typedef struct {
                                    evaluated (its algorithmic work; always filled) */
     int32_t launches;           /* CUDA kernels this count launched */
     int32_t reserved_i;
+    int64_t words_enum;         /* the part of words_r + words_l that belongs to the nodes the
+                                   enumeration kernel evaluates (|L| >= 3; stats) */
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */
@@ -260,6 +262,18 @@ gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uint64_t *tick
  * retired.  Errors: GBC_ERR_ARG (unknown ticket, not serving) and the count's.
  */
 gbc_status gbc_poll(gbc_ctx_t ctx, uint64_t ticket, int timeout_ms, gbc_u128 *out);
+
+/*
+ * gbc_measure_int_peaks -- two microbenchmarks on `device` that scale the
+ * enumeration's roofline (the paper has no counterpart; the benchmark reports
+ * them beside its derived integer peak).  and_popc_words_per_s (host output):
+ * words per second of a register-only loop doing one AND, one POPC and one ADD
+ * per 32-bit word.  l2_bytes_per_s (host output): bytes per second of an
+ * AND + popcount stream over two 16 MiB arrays held in L2 (L1 bypassed).
+ * Allocates 32 MiB of device memory for the duration of the call; takes tens
+ * of milliseconds.  Errors: GBC_ERR_ARG (null output), GBC_ERR_CUDA.
+ */
+gbc_status gbc_measure_int_peaks(int device, double *and_popc_words_per_s, double *l2_bytes_per_s);
 
 /* Human-readable text of a status, and the calling thread's last error. */
 const char *gbc_status_string(gbc_status s);

@@ -71,7 +71,8 @@ class CountInfo(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64),
                 ("ms_candidates", ctypes.c_float), ("ms_pairs", ctypes.c_float),
                 ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32)]
+                ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
+                ("words_enum", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {
@@ -90,6 +91,7 @@ class CountInfo(ctypes.Structure):
             "ms_enumerate": float(self.ms_enumerate),
             "ms_total": float(self.ms_total),
             "enum_words": int(self.enum_words),
+            "words_enum": int(self.words_enum),
             "launches": int(self.launches),
         }
 
@@ -124,6 +126,8 @@ SIGNATURES = {
     "gbc_serve_stop": (ctypes.c_int, [_vp]),
     "gbc_submit": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gbc_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U128)]),
+    "gbc_measure_int_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbc_last_error": (ctypes.c_char_p, []),
 }
@@ -336,3 +340,11 @@ def count_p2_noalloc(n_u: int, n_v: int, off_u, adj_u, off_v, adj_v, q: int, str
                                                ctypes.c_void_p(handle or 0), ctypes.byref(out)),
            "gbc_count_p2_noalloc")
     return out.value()
+
+
+def measure_int_peaks(device: int = 0) -> dict:
+    """Integer-pipe and L2 microbenchmarks on one GPU: words/s of a register-only
+    AND + POPC + ADD loop and bytes/s of an L2-resident AND + popcount stream."""
+    alu, l2 = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().gbc_measure_int_peaks(device, ctypes.byref(alu), ctypes.byref(l2)), "gbc_measure_int_peaks")
+    return {"and_popc_words_per_s": alu.value, "l2_bytes_per_s": l2.value}

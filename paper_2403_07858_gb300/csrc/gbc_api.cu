@@ -767,6 +767,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         }
         inf.words_r = (int64_t)hs.words_r;
         inf.words_l = (int64_t)hs.words_l;
+        inf.words_enum = (int64_t)hs.words_enum;
         if (!J.trivial && J.a.k >= 2) {
             inf.ms_candidates = tm.between(0, 1);
             if (J.a.k >= 3 && J.a.n_cand > 0) {

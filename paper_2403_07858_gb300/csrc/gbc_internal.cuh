@@ -146,6 +146,7 @@ struct SearchStats {
     unsigned long long passed[kMaxPQ + 1];
     unsigned long long words_r;
     unsigned long long words_l;
+    unsigned long long words_enum;  // the part of words_r + words_l of nodes k_enumerate evaluates
 };
 
 // Sets the text gbc_last_error() returns on the calling thread.

@@ -19,7 +19,9 @@ thread_local int t_launches = 0;
 
 // For |L| >= 4 each root also keeps T: for each of its kTPos most shared
 // positions, the bitmap of the candidates containing it (the transpose of the
-// first two word pairs of R), placed after the root's S block.
+// first two word pairs of R), placed after the root's S block.  T is stored
+// word-interleaved: word w of the kTPos rows sits together (kTPos words), so the
+// lanes of a warp that read word w of different rows share cache sectors.
 constexpr int kTPos = 128;
 
 
@@ -343,7 +345,7 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
             const int32_t np = __ldcg(&pm[i]);
             const int64_t x = -1 - v;
             atomicOr(&Rb[2 * ((int64_t)(np >> 6) * c + x) + ((np >> 5) & 1)], 1u << (np & 31));
-            if (Tb && np < kTPos) atomicOr(&Tb[(int64_t)np * WLc + (x >> 5)], 1u << (x & 31));
+            if (Tb && np < kTPos) atomicOr(&Tb[(int64_t)(x >> 5) * kTPos + np], 1u << (x & 31));
         }
     });
     G::sync();
@@ -959,6 +961,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                                     const uint32_t M = LM[e], tg = LT[e];
                                     const int w = (int)(tg & 0xffffu);
                                     const uint4 cy = CRY[tg >> 16];
+                                    const uint32_t *Tw = Tb + (int64_t)w * kTPos;  // word w of every T row
                                     const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
                                     if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
                                     if (m < 16) {
@@ -969,7 +972,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                                             while (bits) {
                                                 const int i = (qw << 5) + __ffs(bits) - 1;
                                                 bits &= bits - 1;
-                                                const uint32_t t = Tb[(int64_t)i * WL + w] & M;
+                                                const uint32_t t = Tw[i] & M;
                                                 const uint32_t c0 = b0 & t;
                                                 b0 ^= t;
                                                 const uint32_t c1 = b1 & c0;
@@ -1061,6 +1064,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     atomicAdd(&a.stats->passed[ell + 1], (unsigned long long)__popc(pm));
                     atomicAdd(&a.stats->words_r, (unsigned long long)got * WRm);
                     atomicAdd(&a.stats->words_l, (unsigned long long)__popc(pm) * WL);
+                    atomicAdd(&a.stats->words_enum, (unsigned long long)got * WRm + (unsigned long long)__popc(pm) * WL);
                 }
             }
             __syncwarp();
@@ -1089,6 +1093,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         atomicAdd(&a.stats->passed[k], st_passed[1]);
         atomicAdd(&a.stats->words_r, st_wr);
         atomicAdd(&a.stats->words_l, st_wl);
+        atomicAdd(&a.stats->words_enum, st_wr + st_wl);
     }
 }
 

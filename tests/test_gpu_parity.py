@@ -113,6 +113,9 @@ def test_tree_statistics_match_oracle(gpu_ctx, p, q, anchor):
         assert info["enum_words"] > 0 and below > 0
     elif k < 4:
         assert info["enum_words"] == 0
+    # the model words of the nodes the enumeration kernel evaluates (|L| >= 3)
+    # are the oracle's words below the roots' children
+    assert info["words_enum"] == (below if k >= 4 else 0)
     assert info["launches"] > 0
     h.close()
 
