@@ -301,13 +301,17 @@ def main():
     # by instruction issue on the integer pipe with its bitmap rows resident in
     # L1/L2, so the roofline is ALU.  Algorithmic work: per evaluated search node
     # ceil(d/32) C_R words, plus ceil(c/32) C_L words for internal nodes, each
-    # word one AND and one POPC; peak: 128 integer lanes per SM per clock.
+    # word one AND and one POPC.  Peak: the POPC pipe, the narrower of the two,
+    # retires 16 results per SM per clock (the register-only AND + POPC loop of
+    # gbc_measure_int_peaks reaches that rate), so the SMs can do at most
+    # SMs x 16 x clock model words per second, two ops each.
     peaks = _peaks()
     roof = None
     if enum_launches and model_words:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_tops = n_sms * 128 * sm_max * 1e6 / 1e12
+        peak_words = n_sms * 16 * sm_max * 1e6
+        peak_tops = 2.0 * peak_words / 1e12
         words_per_launch = sum(model_words.values()) / len(model_words)
         ops_per_launch = 2.0 * words_per_launch
         ms_per_launch = enum_ms / enum_launches
@@ -315,13 +319,16 @@ def main():
         micro = gbc.measure_int_peaks(local)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": _ncu_traffic(), "kernel": "k_enumerate",
-                "peak_source": f"derived: {n_sms} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz max SM clock",
+                "peak_source": f"derived: {n_sms} SMs x 16 POPC/clk/SM x {sm_max:.0f} MHz max SM clock "
+                               "= model words/s, x 2 ops (AND + POPC) per word",
                 "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
                 "model_words_per_launch": words_per_launch,
                 "loaded_words_per_launch": enum_words / enum_launches,
                 "launches": enum_launches, "ms_per_launch": ms_per_launch,
+                "int32_lanes_peak_tops": n_sms * 128 * sm_max * 1e6 / 1e12,
                 "microbench": {
                     "and_popc_add_loop_words_per_s": micro["and_popc_words_per_s"],
+                    "loop_over_derived_peak": micro["and_popc_words_per_s"] / peak_words,
                     "model_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
                                                    / micro["and_popc_words_per_s"],
                     "l2_and_popc_stream_gbs": micro["l2_bytes_per_s"] / 1e9}}
