@@ -721,12 +721,14 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
 //   cursor[lv] (next C_L position to take), dmask[lv] (children still to
 //   enter), span[lv] (pair span of CR[lv]).
 constexpr int kLeafList = 256;  // nonzero leaf words staged per warp before they are expanded
+constexpr int kParents = 64;    // leaf parents per warp (their C_R) whose words may be staged
+constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word index (< 2^24)
 
 struct EnumLayout {
     int wr, wl;     // row capacities in words (both even)
     int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
-    // per warp: CRY (32 x uint4) | leaf masks | leaf tags | levels x (CR | CL | xs) | scalars
-    __host__ __device__ int staging_words() const { return 32 * 4 + 2 * kLeafList; }
+    // per warp: parents (kParents x uint4) | leaf masks | leaf tags | levels x (CR | CL | xs) | scalars
+    __host__ __device__ int staging_words() const { return kParents * 4 + 2 * kLeafList; }
     __host__ __device__ int level_words() const { return wr + wl + 32; }
     __host__ __device__ int warp_words() const {
         return (staging_words() + levels * level_words() + 3 * kMaxPQ + 2 + 3) & ~3;
@@ -809,9 +811,9 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     const CountArgs &a0 = jobs[0];  // holds the batch-wide deadline and status
     uint32_t *wbase = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
                              : smem_stack + (int64_t)wib * lay.warp_words();
-    uint4 *CRY = reinterpret_cast<uint4 *>(wbase);              // C_R of each lane's leaf parent
-    uint32_t *LM = wbase + 32 * 4;                              // staged nonzero leaf words
-    uint32_t *LT = LM + kLeafList;                              // their tags: lane << 16 | word
+    uint4 *PAR = reinterpret_cast<uint4 *>(wbase);              // C_R of the staged leaf parents
+    uint32_t *LM = wbase + kParents * 4;                        // staged nonzero leaf words
+    uint32_t *LT = LM + kLeafList;                              // their tags: slot << kTagShift | word
     uint32_t *base = wbase + lay.staging_words();
     int32_t *cursor = reinterpret_cast<int32_t *>(base + lay.levels * lay.level_words());
     uint32_t *dmask = reinterpret_cast<uint32_t *>(cursor + kMaxPQ);
@@ -855,6 +857,73 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; spanp[0] = sp; }
         }
         __syncwarp();
+        int nl = 0, npar = 0;  // staged leaf words and their parents (warp-uniform)
+        // Phase B over LM[0, n_staged): one staged word (parent y, word w, leaves
+        // M) per lane.  The leaves' counts |C_R(y) & R_x| for all x of the word
+        // are summed bit-sliced: for each position i of C_R(y) the word T_i[w]
+        // of candidates containing i is added into 4-bit vertical counters, and
+        // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.
+        auto count_leaves = [&](int n_staged) {
+            for (int e0 = 0; e0 < n_staged; e0 += 32) {
+                const int e = e0 + lane;
+                if (e < n_staged) {
+                    const uint32_t M = LM[e], tg = LT[e];
+                    const int w = (int)(tg & ((1u << kTagShift) - 1u));
+                    const uint4 cy = PAR[tg >> kTagShift];
+                    const uint32_t *Tw = Tb + (int64_t)w * kTPos;  // word w of every T row
+                    const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
+                    if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
+                    if (m < 16) {
+                        uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
+#pragma unroll
+                        for (int qw = 0; qw < 4; ++qw) {
+                            uint32_t bits = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
+                            while (bits) {
+                                const int i = (qw << 5) + __ffs(bits) - 1;
+                                bits &= bits - 1;
+                                const uint32_t t = Tw[i] & M;
+                                const uint32_t c0 = b0 & t;
+                                b0 ^= t;
+                                const uint32_t c1 = b1 & c0;
+                                b1 ^= c0;
+                                const uint32_t c2 = b2 & c1;
+                                b2 ^= c1;
+                                b3 ^= c2;
+                            }
+                        }
+                        words += m + 1;
+                        for (int v = kq; v <= m; ++v) {
+                            const uint32_t eq = M & ((v & 1) ? b0 : ~b0) & ((v & 2) ? b1 : ~b1) &
+                                                ((v & 4) ? b2 : ~b2) & ((v & 8) ? b3 : ~b3);
+                            const int cnt = __popc(eq);
+                            if (cnt) {
+                                if (STATS) st_passed[1] += cnt;
+                                const ulonglong2 bc = (smem_binom && v < kSmemBinom)
+                                                          ? s_binom[v] : binom_lookup(a.binom, kq, v, ovf);
+                                add_u128(unit_acc, (u128)bc.x * (unsigned)cnt, ovf);
+                            }
+                        }
+                    } else {
+                        // a wide C_R(y): the leaves one by one (C_R(y) has bits in
+                        // its second word pair only if R has two pairs)
+                        const bool two = (cy.z | cy.w) != 0u;
+                        uint32_t bits = M;
+                        while (bits) {
+                            const int32_t x = (w << 5) + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            int nx = popc2(make_uint2(cy.x, cy.y), Rp[x]);
+                            if (two) nx += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
+                            words += two ? 4 : 2;
+                            if (nx >= kq) {
+                                if (STATS) st_passed[1] += 1;
+                                if (smem_binom && nx < kSmemBinom) add_u128(unit_acc, s_binom[nx], ovf);
+                                else add_u128(unit_acc, binom_lookup(a.binom, kq, nx, ovf), ovf);
+                            }
+                        }
+                    }
+                }
+            }
+        };
         int lv = 0;
         unsigned batches = 0;
         while (true) {
@@ -903,16 +972,19 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             const uint32_t *cl = CL(lv);
             if (ell + 2 == k) {
                 // Children y are leaf parents.  Phase A: each lane forms C_R(y) =
-                // C_R & R_y (kept in CRY) and stages the nonzero words of its
-                // leaf set C_L & S_y (after y) in the warp's list.  Phase B: the
-                // staged leaves are dealt out 32 at a time, whatever parent they
-                // belong to, so every lane evaluates a leaf on every step.
+                // C_R & R_y; a child that passes puts it in the warp's parent list
+                // and stages the nonzero words of its leaf set C_L & S_y (after y)
+                // in the warp's leaf-word list.  Phase B (count_leaves) deals the
+                // staged words out 32 at a time, whatever parent, node or batch
+                // they come from, so every lane evaluates leaves on every step.
+                // The lists carry over from batch to batch and node to node of
+                // the unit and are expanded when full or when the unit ends.
                 int32_t y = 0;
                 bool py = false;
+                uint4 cy = make_uint4(0, 0, 0, 0);
                 if (lane < got) {
                     y = XS(lv)[lane];
                     int ny = 0;
-                    uint4 cy = make_uint4(0, 0, 0, 0);
                     if (sp <= 2) {
                         if (sp > 0) { const uint2 v = and2(cr[0], Rp[y]); cy.x = v.x; cy.y = v.y; }
                         if (sp > 1) { const uint2 v = and2(cr[1], Rp[c + y]); cy.z = v.x; cy.w = v.y; }
@@ -920,7 +992,6 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     } else {
                         for (int pw = 0; pw < sp; ++pw) ny += popc2(cr[pw], Rp[pw * c + y]);
                     }
-                    CRY[lane] = cy;
                     py = ny >= kq;
                     words += 2 * sp;
                 }
@@ -936,84 +1007,29 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 const int lo_y = (y + 1) >> 5;
                 const int lo_min = (__shfl_sync(kFull, y, 0) + 1) >> 5;  // lane 0 holds the smallest y
                 if (sp <= 2) {
-                    int nl = 0;
-                    for (int w = lo_min; w < WL; ++w) {
-                        uint32_t mk = 0;
-                        if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; words += 1; }
-                        const unsigned nz = __ballot_sync(kFull, mk != 0u);
-                        if (mk) {
-                            const int at = nl + __popc(nz & ((1u << lane) - 1u));
-                            LM[at] = mk;
-                            LT[at] = ((uint32_t)lane << 16) | (uint32_t)w;
-                        }
-                        nl += __popc(nz);
-                        if (nl > kLeafList - 32 || (w + 1 == WL && nl > 0)) {
-                            __syncwarp();
-                            // Phase B over LM[0, nl): one staged word (parent y, word w,
-                            // leaves M) per lane.  The leaves' counts |C_R(y) & R_x|
-                            // for all x of the word are summed bit-sliced: for each
-                            // position i of C_R(y) the word T_i[w] of candidates
-                            // containing i is added into 4-bit vertical counters, and
-                            // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.
-                            for (int e0 = 0; e0 < nl; e0 += 32) {
-                                const int e = e0 + lane;
-                                if (e < nl) {
-                                    const uint32_t M = LM[e], tg = LT[e];
-                                    const int w = (int)(tg & 0xffffu);
-                                    const uint4 cy = CRY[tg >> 16];
-                                    const uint32_t *Tw = Tb + (int64_t)w * kTPos;  // word w of every T row
-                                    const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
-                                    if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
-                                    if (m < 16) {
-                                        uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
-#pragma unroll
-                                        for (int qw = 0; qw < 4; ++qw) {
-                                            uint32_t bits = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
-                                            while (bits) {
-                                                const int i = (qw << 5) + __ffs(bits) - 1;
-                                                bits &= bits - 1;
-                                                const uint32_t t = Tw[i] & M;
-                                                const uint32_t c0 = b0 & t;
-                                                b0 ^= t;
-                                                const uint32_t c1 = b1 & c0;
-                                                b1 ^= c0;
-                                                const uint32_t c2 = b2 & c1;
-                                                b2 ^= c1;
-                                                b3 ^= c2;
-                                            }
-                                        }
-                                        words += m + 1;
-                                        for (int v = kq; v <= m; ++v) {
-                                            const uint32_t eq = M & ((v & 1) ? b0 : ~b0) & ((v & 2) ? b1 : ~b1) &
-                                                                ((v & 4) ? b2 : ~b2) & ((v & 8) ? b3 : ~b3);
-                                            const int cnt = __popc(eq);
-                                            if (cnt) {
-                                                if (STATS) st_passed[1] += cnt;
-                                                const ulonglong2 bc = (smem_binom && v < kSmemBinom)
-                                                                          ? s_binom[v] : binom_lookup(a.binom, kq, v, ovf);
-                                                add_u128(unit_acc, (u128)bc.x * (unsigned)cnt, ovf);
-                                            }
-                                        }
-                                    } else {
-                                        // a wide C_R(y): the leaves one by one
-                                        uint32_t bits = M;
-                                        while (bits) {
-                                            const int32_t x = (w << 5) + __ffs(bits) - 1;
-                                            bits &= bits - 1;
-                                            int n = popc2(make_uint2(cy.x, cy.y), Rp[x]);
-                                            if (sp > 1) n += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
-                                            words += 2 * sp;
-                                            if (n >= kq) {
-                                                if (STATS) st_passed[1] += 1;
-                                                if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
-                                                else add_u128(unit_acc, binom_lookup(a.binom, kq, n, ovf), ovf);
-                                            }
-                                        }
-                                    }
-                                }
+                    if (lo_min < WL) {  // else no child has a leaf after it
+                        const unsigned pm = __ballot_sync(kFull, py);
+                        const int slot = npar + __popc(pm & ((1u << lane) - 1u));
+                        if (py) PAR[slot] = cy;
+                        npar += __popc(pm);  // <= kParents: at most kParents - 32 before the batch
+                        for (int w = lo_min; w < WL; ++w) {
+                            uint32_t mk = 0;
+                            if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; words += 1; }
+                            const unsigned nz = __ballot_sync(kFull, mk != 0u);
+                            if (mk) {
+                                const int at = nl + __popc(nz & ((1u << lane) - 1u));
+                                LM[at] = mk;
+                                LT[at] = ((uint32_t)slot << kTagShift) | (uint32_t)w;
                             }
-                            nl = 0;
-                            __syncwarp();
+                            nl += __popc(nz);
+                            const bool last = w + 1 == WL;
+                            if (nl > kLeafList - 32 || (last && npar > kParents - 32)) {
+                                __syncwarp();
+                                count_leaves(nl);
+                                nl = 0;
+                                if (last) npar = 0;  // every parent's words are staged and counted
+                                __syncwarp();
+                            }
                         }
                     }
                 } else if (py) {
@@ -1071,6 +1087,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (lane == 0) dmask[lv] = dmb;
             __syncwarp();
         }
+        if (nl > 0) count_leaves(nl);  // the unit's last staged words
+        __syncwarp();
         // the unit's sum goes to its job (and to its root when split by root)
         const u128 s = warp_sum_u128(unit_acc, ovf);
 #pragma unroll
@@ -1128,6 +1146,7 @@ cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const i
                              bool stats, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
                              cudaStream_t st) {
     EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3)};
+    if (max_wl >= (1 << kTagShift)) return cudaErrorInvalidValue;  // staged-word tags hold the word index in 24 bits
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;
     const size_t smem = per_warp * warps_per_cta;
