@@ -720,7 +720,7 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
 //   CR[lv] : wr words, CL[lv] : wl words, xs[lv] : 32 child ids;
 //   cursor[lv] (next C_L position to take), dmask[lv] (children still to
 //   enter), span[lv] (pair span of CR[lv]).
-constexpr int kLeafList = 256;  // nonzero leaf words staged per warp before they are expanded
+constexpr int kLeafList = 128;  // nonzero leaf words staged per warp before they are expanded
 constexpr int kParents = 64;    // leaf parents per warp (their C_R) whose words may be staged
 constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word index (< 2^24)
 
@@ -878,14 +878,23 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
 #pragma unroll
                         for (int qw = 0; qw < 4; ++qw) {
                             uint32_t bits = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
+                            // two positions per step: a carry-save add of both T words
+                            // (sum into b0, majority carry into b1..b3); the leaf mask M
+                            // is applied once, when the counts are read
                             while (bits) {
-                                const int i = (qw << 5) + __ffs(bits) - 1;
+                                const int i1 = (qw << 5) + __ffs(bits) - 1;
                                 bits &= bits - 1;
-                                const uint32_t t = Tw[i] & M;
-                                const uint32_t c0 = b0 & t;
-                                b0 ^= t;
-                                const uint32_t c1 = b1 & c0;
-                                b1 ^= c0;
+                                const uint32_t t1 = Tw[i1];
+                                uint32_t t2 = 0u;
+                                if (bits) {
+                                    const int i2 = (qw << 5) + __ffs(bits) - 1;
+                                    bits &= bits - 1;
+                                    t2 = Tw[i2];
+                                }
+                                const uint32_t cy2 = (b0 & t1) | (b0 & t2) | (t1 & t2);
+                                b0 ^= t1 ^ t2;
+                                const uint32_t c1 = b1 & cy2;
+                                b1 ^= cy2;
                                 const uint32_t c2 = b2 & c1;
                                 b2 ^= c1;
                                 b3 ^= c2;
@@ -1005,9 +1014,9 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     }
                 }
                 const int lo_y = (y + 1) >> 5;
-                const int lo_min = (__shfl_sync(kFull, y, 0) + 1) >> 5;  // lane 0 holds the smallest y
+                const int lo_min = __reduce_min_sync(kFull, py ? lo_y : (int)WL);  // first word any passing child stages
                 if (sp <= 2) {
-                    if (lo_min < WL) {  // else no child has a leaf after it
+                    if (lo_min < WL) {  // else no passing child has a leaf after it
                         const unsigned pm = __ballot_sync(kFull, py);
                         const int slot = npar + __popc(pm & ((1u << lane) - 1u));
                         if (py) PAR[slot] = cy;
@@ -1053,6 +1062,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     }
                 }
                 __syncwarp();
+                if (cur >= c) {  // every child taken: back to the parent at once
+                    if (lv == 0) break;
+                    --lv;
+                }
                 continue;  // no child to enter: the next batch of this node
             }
             // internal children: evaluate both pruning tests, flag those to enter
