@@ -433,6 +433,7 @@ struct Job {
     CountArgs a;
     Small h;
     bool trivial = false;
+    size_t scratch_bytes = 0;  // device scratch held while this job ran
     gbc_status st = GBC_OK;
     char err[256] = "";
     void set_error(gbc_status s, const char *fmt, ...) {
@@ -700,7 +701,10 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             // the job table is read by the launch: keep the host copy alive until it has run
             CK(cudaStreamSynchronize(st));
         }
+        for (int i : wave) jobs[i].scratch_bytes = sc.bytes + wave_sc.bytes;
     }
+    for (Job &J : jobs)
+        if (J.scratch_bytes == 0) J.scratch_bytes = sc.bytes;
     tm.mark(3, st);
     CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
     if (d_stats && hs_out) CK(cudaMemcpyAsync(hs_out, d_stats, sizeof(SearchStats), cudaMemcpyDeviceToHost, st));
@@ -768,6 +772,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         inf.words_r = (int64_t)hs.words_r;
         inf.words_l = (int64_t)hs.words_l;
         inf.words_enum = (int64_t)hs.words_enum;
+        inf.scratch_bytes = (int64_t)J.scratch_bytes;
         if (!J.trivial && J.a.k >= 2) {
             inf.ms_candidates = tm.between(0, 1);
             if (J.a.k >= 3 && J.a.n_cand > 0) {

@@ -117,6 +117,8 @@ def test_tree_statistics_match_oracle(gpu_ctx, p, q, anchor):
     # are the oracle's words below the roots' children
     assert info["words_enum"] == (below if k >= 4 else 0)
     assert info["launches"] > 0
+    if k >= 2:
+        assert info["scratch_bytes"] > 0
     h.close()
 
 
