@@ -545,17 +545,26 @@ def serve_workload(args, rank, world, local):
     ctx.close()
 
 
+def kernel_source_digest() -> str:
+    """SHA-256 of the enumeration kernels' source with comments and whitespace
+    removed: it changes when the code does, not when a comment does."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2403_07858_gb300", "csrc", "gbc_search.cu")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return hashlib.sha256("".join(src.split()).encode()).hexdigest()
+
+
 def _ncu_traffic():
     """dram bytes per launch of the enumeration kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    summary, if it was taken on the current kernel code; else None."""
     path = os.path.join(ROOT, "profiles", "enumerate_traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
         return None
-    import hashlib
-    src = open(os.path.join(ROOT, "paper_2403_07858_gb300", "csrc", "gbc_search.cu"), "rb").read()
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("source_digest") != kernel_source_digest():
         return None
     return rec.get("dram_bytes_per_launch_scaled")
 

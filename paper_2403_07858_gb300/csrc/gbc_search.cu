@@ -706,20 +706,25 @@ cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
 // parent's C_R and C_L, which sit in shared memory and are read by every lane
 // at once (the siblings-share-the-parent idea of Sec. IV's hybrid search).
 //
-// At a node two levels above the leaves (|L| = k - 2) each lane finishes its
-// child y on its own: C_R(y) = C_R & R_y stays in registers and the lane walks
-// the leaves x in C_L & S_y after y, adding C(|C_R(y) & R_x|, kq) for each
-// that reaches kq (Alg. 1's last two levels, one subtree per lane).
-// Internal children that pass both pruning tests (|C_R'| >= kq, |C_L'| >=
-// k - |L'|) are entered one by one, their C_R' and C_L' rebuilt cooperatively.
+// At a node two levels above the leaves (|L| = k - 2) the warp does not enter
+// its children y (the leaf parents).  Each lane forms C_R(y) = C_R & R_y; a
+// child that reaches kq takes a slot in the warp's parent list and stages the
+// nonzero words of its leaves C_L & S_y (after y) in the warp's leaf-word list.
+// The staged words are expanded 32 at a time (count_leaves): for each word,
+// the counts |C_R(y) & R_x| of its up to 32 leaves x are summed bit-sliced from
+// the root's T block and C(count, kq) is added per leaf (Alg. 1's last two
+// levels).  Internal children that pass both pruning tests (|C_R'| >= kq,
+// |C_L'| >= k - |L'|) are entered one by one, their C_R' and C_L' rebuilt
+// cooperatively.
 //
 // C_R is read only up to its span (word pairs holding its set bits); thanks to
 // the per-root position order, spans are one pair deep in most of the tree.
 //
-// Per warp, for each level lv = |L| - 2 in [0, k-3):
-//   CR[lv] : wr words, CL[lv] : wl words, xs[lv] : 32 child ids;
-//   cursor[lv] (next C_L position to take), dmask[lv] (children still to
-//   enter), span[lv] (pair span of CR[lv]).
+// Per warp: the parent list (kParents C_R(y) as uint4), the leaf-word list
+// (kLeafList words and their tags) and, for each level lv = |L| - 2 in
+// [0, k-3): CR[lv] : wr words, CL[lv] : wl words, xs[lv] : 32 child ids;
+// cursor[lv] (next C_L position to take), dmask[lv] (children still to
+// enter), span[lv] (pair span of CR[lv]).
 constexpr int kLeafList = 128;  // nonzero leaf words staged per warp before they are expanded
 constexpr int kParents = 64;    // leaf parents per warp (their C_R) whose words may be staged
 constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word index (< 2^24)
