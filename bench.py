@@ -570,14 +570,19 @@ def _ncu_traffic():
 
 
 def _auto_anchor(g, k):
-    """The library's anchor rule for p = q = k: the side whose own degrees give
-    the smaller sum of C(deg, 2) (the oracle counts the same from either side)."""
+    """The library's anchor rule for p = q = k (the oracle counts the same from
+    either side): up to k = 4 the side whose 2-hop wedges through the other side
+    are fewer, from k = 5 the side with the lighter own degree tail."""
     import numpy as np
     du = np.diff(g.off_u).astype(np.int64)
     dv = np.diff(g.off_v).astype(np.int64)
     if k == 1:
         return "U"
-    return "U" if int((du * (du - 1) // 2).sum()) <= int((dv * (dv - 1) // 2).sum()) else "V"
+    wedges_u = int((du * (du - 1) // 2).sum())  # wedges centred on U vertices
+    wedges_v = int((dv * (dv - 1) // 2).sum())
+    if k <= 4:
+        return "U" if wedges_v <= wedges_u else "V"
+    return "U" if wedges_u <= wedges_v else "V"
 
 
 def reference_arm(args, pqs):
