@@ -85,6 +85,11 @@ void gbc_ctx_destroy(gbc_ctx_t ctx);
  *   nU, nV            vertex counts (>= 0)
  *   offU [nU+1], adjU [|E|]   U -> V adjacency (host)
  *   offV [nV+1], adjV [|E|]   V -> U adjacency (host), the transpose of U's
+ * After validation the library renumbers each side by descending degree (ties
+ * in the caller's order) for memory locality; the priority order (degree, id)
+ * and so every count, per-root split and root range are the caller's, and every
+ * vertex id this interface takes or returns is the caller's.  The renumbering
+ * runs on the host, O(|U| + |V| + |E|).
  * The graph handle owns its device memory until gbc_free_graph.
  * Errors: GBC_ERR_ARG, GBC_ERR_INVALID_GRAPH, GBC_ERR_OOM, GBC_ERR_CUDA.
  */
@@ -94,7 +99,8 @@ gbc_status gbc_load_graph(gbc_ctx_t ctx, int32_t nU, int32_t nV,
                           gbc_graph_t *out);
 
 /* As gbc_load_graph, but the four arrays are device pointers (borrowed; the
- * graph keeps its own copy). */
+ * graph keeps its own copy).  The renumbering copies the U side's arrays and
+ * V's offsets to the host once. */
 gbc_status gbc_load_graph_device(gbc_ctx_t ctx, int32_t nU, int32_t nV,
                                  const int32_t *offU_d, const int32_t *adjU_d,
                                  const int32_t *offV_d, const int32_t *adjV_d,

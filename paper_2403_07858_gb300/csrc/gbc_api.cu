@@ -104,6 +104,8 @@ struct gbc_graph_s {
     ulonglong2 *binom = nullptr;
     int32_t *n_ovf = nullptr;
     int32_t binom_nmax = 0;
+    int32_t *callerU = nullptr, *callerV = nullptr;  // caller's id of every (renumbered) vertex
+    std::vector<int32_t> callerU_h, callerV_h;
 };
 
 // Stream-ordered scratch that is released when the owner goes out of scope.
@@ -190,7 +192,7 @@ void gbc_free_graph(gbc_graph_t g) {
     cudaSetDevice(g->ctx->device);
     cudaStream_t st = g->ctx->lane.st;
     void *ps[] = {g->offU, g->adjU, g->offV, g->adjV, g->degU, g->degV, g->adjV_byU,
-                  g->mirrorU, g->adjU_byV, g->mirrorV, g->binom, g->n_ovf};
+                  g->mirrorU, g->adjU_byV, g->mirrorV, g->binom, g->n_ovf, g->callerU, g->callerV};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, st);
     cudaStreamSynchronize(st);
@@ -221,6 +223,58 @@ gbc_status gbc_graph_info(gbc_graph_t g, int32_t *nU, int32_t *nV, int64_t *nE, 
 
 // ---------------------------------------------------------------------------
 // graph loading
+// Renumbering at load time: each side by descending degree, ties in the
+// caller's order.  Hubs' rows then sit together, which shortens the 2-hop
+// expansion's reach through memory (the global-id reordering of Sec. V-B,
+// Border, has the same aim; the bitmaps here are per root, so only locality
+// is at stake).  Because ties keep the caller's order, the rank order
+// (degree, id) of Def. 2 is unchanged and every search tree is the caller's.
+// Two counting-sort passes build the renumbered CSRs with sorted rows: V rows
+// by walking the new U order, then U rows by walking the new V order.
+static void order_by_degree(int32_t n, const int32_t *off, std::vector<int32_t> &fresh, std::vector<int32_t> &caller) {
+    int32_t maxd = 0;
+    for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, off[v + 1] - off[v]);
+    std::vector<int64_t> start((size_t)maxd + 1, 0);
+    for (int32_t v = 0; v < n; ++v) start[off[v + 1] - off[v]] += 1;
+    int64_t run = 0;
+    for (int32_t d = maxd; d >= 0; --d) {
+        const int64_t c = start[d];
+        start[d] = run;
+        run += c;
+    }
+    fresh.resize(n);
+    caller.resize(n);
+    for (int32_t v = 0; v < n; ++v) {
+        const int32_t nv = (int32_t)start[off[v + 1] - off[v]]++;
+        fresh[v] = nv;
+        caller[nv] = v;
+    }
+}
+
+static void renumber_by_degree(int32_t nU, int32_t nV, const int32_t *offU, const int32_t *adjU, const int32_t *offV,
+                               std::vector<int32_t> &offU2, std::vector<int32_t> &adjU2, std::vector<int32_t> &offV2,
+                               std::vector<int32_t> &adjV2, std::vector<int32_t> &callerU,
+                               std::vector<int32_t> &callerV) {
+    std::vector<int32_t> freshU, freshV;
+    order_by_degree(nU, offU, freshU, callerU);
+    order_by_degree(nV, offV, freshV, callerV);
+    const int64_t E = offU[nU];
+    offU2.assign((size_t)nU + 1, 0);
+    offV2.assign((size_t)nV + 1, 0);
+    adjU2.resize((size_t)E);
+    adjV2.resize((size_t)E);
+    for (int32_t v = 0; v < nV; ++v) offV2[v + 1] = offV2[v] + (offV[callerV[v] + 1] - offV[callerV[v]]);
+    for (int32_t u = 0; u < nU; ++u) offU2[u + 1] = offU2[u] + (offU[callerU[u] + 1] - offU[callerU[u]]);
+    std::vector<int32_t> cur(offV2.begin(), offV2.end() - 1);
+    for (int32_t u = 0; u < nU; ++u) {
+        const int32_t uo = callerU[u];
+        for (int32_t e = offU[uo]; e < offU[uo + 1]; ++e) adjV2[cur[freshV[adjU[e]]]++] = u;
+    }
+    cur.assign(offU2.begin(), offU2.end() - 1);
+    for (int32_t v = 0; v < nV; ++v)
+        for (int32_t e = offV2[v]; e < offV2[v + 1]; ++e) adjU2[cur[adjV2[e]]++] = v;
+}
+
 static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU,
                               const int32_t *adjU, const int32_t *offV, const int32_t *adjV, bool host,
                               gbc_graph_t *out) {
@@ -308,6 +362,36 @@ static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32
                           : (h_status & kStUnsorted) ? "row not strictly increasing"
                                                      : "V-side CSR is not the transpose of the U side";
         return cleanup(fail(GBC_ERR_INVALID_GRAPH, "gbc_load_graph: %s", why));
+    }
+    // renumber both sides by degree (on the host) and replace the device copies
+    {
+        std::vector<int32_t> hoffU, hadjU, hoffV, hadjV;
+        const int32_t *pOffU = offU, *pAdjU = adjU, *pOffV = offV;
+        if (!host) {
+            hoffU.resize((size_t)nU + 1);
+            hoffV.resize((size_t)nV + 1);
+            hadjU.resize(std::max<size_t>(E, 1));
+            CKG(cudaMemcpyAsync(hoffU.data(), g->offU, ((size_t)nU + 1) * 4, cudaMemcpyDeviceToHost, st));
+            CKG(cudaMemcpyAsync(hoffV.data(), g->offV, ((size_t)nV + 1) * 4, cudaMemcpyDeviceToHost, st));
+            if (E) CKG(cudaMemcpyAsync(hadjU.data(), g->adjU, E * 4, cudaMemcpyDeviceToHost, st));
+            CKG(cudaStreamSynchronize(st));
+            pOffU = hoffU.data();
+            pAdjU = hadjU.data();
+            pOffV = hoffV.data();
+        }
+        std::vector<int32_t> offU2, adjU2, offV2, adjV2;
+        renumber_by_degree(nU, nV, pOffU, pAdjU, pOffV, offU2, adjU2, offV2, adjV2, g->callerU_h, g->callerV_h);
+        CKG(cudaMemcpyAsync(g->offU, offU2.data(), ((size_t)nU + 1) * 4, cudaMemcpyHostToDevice, st));
+        CKG(cudaMemcpyAsync(g->offV, offV2.data(), ((size_t)nV + 1) * 4, cudaMemcpyHostToDevice, st));
+        if (E) {
+            CKG(cudaMemcpyAsync(g->adjU, adjU2.data(), E * 4, cudaMemcpyHostToDevice, st));
+            CKG(cudaMemcpyAsync(g->adjV, adjV2.data(), E * 4, cudaMemcpyHostToDevice, st));
+        }
+        CKG(cudaMallocAsync((void **)&g->callerU, std::max<size_t>(nU, 1) * 4, st));
+        CKG(cudaMallocAsync((void **)&g->callerV, std::max<size_t>(nV, 1) * 4, st));
+        if (nU) CKG(cudaMemcpyAsync(g->callerU, g->callerU_h.data(), (size_t)nU * 4, cudaMemcpyHostToDevice, st));
+        if (nV) CKG(cudaMemcpyAsync(g->callerV, g->callerV_h.data(), (size_t)nV * 4, cudaMemcpyHostToDevice, st));
+        CKG(cudaStreamSynchronize(st));  // the host vectors go out of scope
     }
     // degrees, per-side rank-sorted rows and mirror positions
     CKG(cudaMallocAsync((void **)&g->degU, std::max<size_t>(nU, 1) * 4, st));
@@ -493,11 +577,13 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         CountArgs &a = J.a;
         memset(&a, 0, sizeof a);
         if (J.anchor == GBC_ANCHOR_U) {
-            a.g = SideView{g->nU, g->nV, g->offU, g->adjU, g->offV, g->adjV_byU, g->mirrorU, g->degU, g->maxdegU};
+            a.g = SideView{g->nU, g->nV, g->offU, g->adjU, g->offV, g->adjV_byU, g->mirrorU, g->degU, g->maxdegU,
+                           g->callerU};
             a.k = J.p;
             a.kq = J.q;
         } else {
-            a.g = SideView{g->nV, g->nU, g->offV, g->adjV, g->offU, g->adjU_byV, g->mirrorV, g->degV, g->maxdegV};
+            a.g = SideView{g->nV, g->nU, g->offV, g->adjV, g->offU, g->adjU_byV, g->mirrorV, g->degV, g->maxdegV,
+                           g->callerV};
             a.k = J.q;
             a.kq = J.p;
         }
@@ -852,9 +938,16 @@ extern "C" gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor
     CK(cudaMemsetAsync(d, 0, (size_t)std::max<int64_t>(nA, 1) * 16, st));
     gbc_status s = count_impl(g, p, q, nullptr, total, nullptr, anchor, d);
     if (s == GBC_OK && nA > 0) {
-        cudaError_t e = cudaMemcpyAsync(per_root, d, (size_t)nA * 16, cudaMemcpyDeviceToHost, st);
+        // per library id on the device; the caller's ids on the host
+        std::vector<gbc_u128> tmp((size_t)nA);
+        cudaError_t e = cudaMemcpyAsync(tmp.data(), d, (size_t)nA * 16, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) s = fail(GBC_ERR_CUDA, "gbc_count_per_root: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            s = fail(GBC_ERR_CUDA, "gbc_count_per_root: %s", cudaGetErrorString(e));
+        } else {
+            const std::vector<int32_t> &caller = anchor == GBC_ANCHOR_U ? g->callerU_h : g->callerV_h;
+            for (int64_t i = 0; i < nA; ++i) per_root[caller[i]] = tmp[i];
+        }
     }
     cudaFreeAsync(d, st);
     cudaStreamSynchronize(st);

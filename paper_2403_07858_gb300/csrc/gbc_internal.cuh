@@ -25,7 +25,9 @@ enum : uint32_t {
 };
 
 // The graph seen from one anchor side A (the side whose vertices root the
-// search trees); O is the other side.  Vertex ids are the caller's ids.
+// search trees); O is the other side.  Vertex ids are the library's: each side
+// renumbered by descending degree at load time, ties in the caller's order, so
+// the rank order (degree, id) is the caller's; callerA maps back.
 struct SideView {
     int32_t nA, nO;
     const int32_t *offA, *adjA;   // A -> O, rows sorted by O id
@@ -34,6 +36,7 @@ struct SideView {
     const int32_t *mirror;        // per A-edge e = (a, o): index of a in adjO_rank row of o
     const int32_t *degA;          // degree of every A vertex
     int32_t maxdegA;
+    const int32_t *callerA;       // the caller's id of every A vertex
 };
 
 // Rank key of Def. 2 (reading: degree first, ties by id), ascending.

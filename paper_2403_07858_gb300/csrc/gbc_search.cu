@@ -33,7 +33,8 @@ __global__ void k_single_vertex_sets(CountArgs a) {
     const int64_t n = a.g.nA;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((n + 31) / 32) * 32;
          i += (int64_t)gridDim.x * blockDim.x) {
-        if (i < n && i >= a.root_begin && i < a.root_end) {
+        const int64_t ic = i < n ? a.g.callerA[i] : -1;  // root ranges are in the caller's ids
+        if (i < n && ic >= a.root_begin && ic < a.root_end) {
             bool o = false;
             ulonglong2 v = binom_lookup(a.binom, a.kq, a.g.degA[i], o);
             if (a.per_root) {
@@ -87,7 +88,8 @@ __global__ void k_root_omega(CountArgs a) {
             }
         }
         a.omega[u] = (int32_t)om;
-        const bool mine = u >= a.root_begin && u < a.root_end;
+        const int32_t uc = g.callerA[u];  // root ranges are in the caller's ids
+        const bool mine = uc >= a.root_begin && uc < a.root_end;
         if (mine && om >= (int64_t)(a.k - 1) * a.kq && om > 0) {
             const int tier = om <= kWarpTierOmega ? 0 : (om <= kCtaTierOmega ? 1 : 2);
             const int slot = atomicAdd(&a.tier_count[tier], 1);

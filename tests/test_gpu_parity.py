@@ -225,6 +225,14 @@ def test_device_arrays_load(gpu_ctx):
     arrs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (g.off_u, g.adj_u, g.off_v, g.adj_v)]
     h = gpu_ctx.load_graph(g.n_u, g.n_v, *arrs)
     assert h.count(3, 3) == oracle.count(g, 3, 3)
+    # the library renumbers vertices internally; per-root results come back
+    # in the caller's ids, the same from device or host arrays
+    hh = gpu_ctx.load(g)
+    for anchor in ("U", "V"):
+        tot_d, per_d = h.count_per_root(3, 3, anchor)
+        tot_h, per_h = hh.count_per_root(3, 3, anchor)
+        assert tot_d == tot_h and list(per_d) == list(per_h)
+    hh.close()
     h.close()
 
 
