@@ -246,9 +246,8 @@ def main():
             step_ms.append(e0.elapsed_time(e1))
             for info in infos:
                 launches += info["launches"]
-                if info["enum_words"] > 0:
+                if info["set_size"] >= 4 and info["ms_enumerate"] > 0:
                     enum_ms += info["ms_enumerate"]
-                    enum_words += info["enum_words"]
                     enum_launches += 1
     clocks = clk.summary()
     # Algorithmic work of the enumeration launches (untimed): the model words
@@ -261,6 +260,7 @@ def main():
         assert n == ref_counts[k]
         if sinfo["words_enum"] > 0:
             model_words[k] = sinfo["words_enum"]
+            enum_words += sinfo["enum_words"]
     h.close()
     ms_step = statistics.mean(step_ms)
     if dist is not None:
@@ -323,7 +323,7 @@ def main():
                                "= model words/s, x 2 ops (AND + POPC) per word",
                 "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
                 "model_words_per_launch": words_per_launch,
-                "loaded_words_per_launch": enum_words / enum_launches,
+                "loaded_words_per_launch": enum_words / len(model_words),
                 "launches": enum_launches, "ms_per_launch": ms_per_launch,
                 "int32_lanes_peak_tops": n_sms * 128 * sm_max * 1e6 / 1e12,
                 "microbench": {

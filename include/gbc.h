@@ -151,8 +151,8 @@ typedef struct {
     float ms_pairs;             /* device time: pairwise rows (C_L bitmaps) */
     float ms_enumerate;         /* device time: enumeration kernel */
     float ms_total;             /* device time of the whole count */
-    int64_t enum_words;         /* C_R + C_L words of the children the enumeration kernel
-                                   evaluated (its algorithmic work; always filled) */
+    int64_t enum_words;         /* words the enumeration kernel actually loaded for the
+                                   children it evaluated (C_R read up to its span; stats) */
     int32_t launches;           /* CUDA kernels this count launched */
     int32_t reserved_i;
     int64_t words_enum;         /* the part of words_r + words_l that belongs to the nodes the

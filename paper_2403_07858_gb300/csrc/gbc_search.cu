@@ -842,7 +842,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         if (__shfl_sync(kFull, (int)past_deadline(a), 0)) continue;  // this job ran out of time: drop its units
         const int k = a.k, kq = a.kq;
         const bool smem_binom = kq == kq0;
-        unsigned long long words = 0;  // words this lane loaded for children (span-truncated)
+        unsigned long long words = 0;  // words this lane loaded for children (span-truncated; statistics only)
         const int64_t gidx = unit.y;
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
@@ -907,7 +907,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                                 b3 ^= c2;
                             }
                         }
-                        words += m + 1;
+                        if (STATS) words += m + 1;
                         for (int v = kq; v <= m; ++v) {
                             const uint32_t eq = M & ((v & 1) ? b0 : ~b0) & ((v & 2) ? b1 : ~b1) &
                                                 ((v & 4) ? b2 : ~b2) & ((v & 8) ? b3 : ~b3);
@@ -929,7 +929,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                             bits &= bits - 1;
                             int nx = popc2(make_uint2(cy.x, cy.y), Rp[x]);
                             if (two) nx += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
-                            words += two ? 4 : 2;
+                            if (STATS) words += two ? 4 : 2;
                             if (nx >= kq) {
                                 if (STATS) st_passed[1] += 1;
                                 if (smem_binom && nx < kSmemBinom) add_u128(unit_acc, s_binom[nx], ovf);
@@ -1009,7 +1009,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                         for (int pw = 0; pw < sp; ++pw) ny += popc2(cr[pw], Rp[pw * c + y]);
                     }
                     py = ny >= kq;
-                    words += 2 * sp;
+                    if (STATS) words += 2 * sp;
                 }
                 if (STATS) {
                     const unsigned pm = __ballot_sync(kFull, py);
@@ -1030,7 +1030,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                         npar += __popc(pm);  // <= kParents: at most kParents - 32 before the batch
                         for (int w = lo_min; w < WL; ++w) {
                             uint32_t mk = 0;
-                            if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; words += 1; }
+                            if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; if (STATS) words += 1; }
                             const unsigned nz = __ballot_sync(kFull, mk != 0u);
                             if (mk) {
                                 const int at = nl + __popc(nz & ((1u << lane) - 1u));
@@ -1052,13 +1052,13 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     // wide C_R (rare): the lane walks its own leaves, C_R(y) & R_x re-read per leaf
                     for (int w = lo_y; w < WL; ++w) {
                         uint32_t bits = cl[w] & St[(int64_t)w * c + y];
-                        words += 1;
+                        if (STATS) words += 1;
                         while (bits) {
                             const int32_t x = (w << 5) + __ffs(bits) - 1;
                             bits &= bits - 1;
                             int n = 0;
                             for (int pw = 0; pw < sp; ++pw) n += popc2(and2(cr[pw], Rp[pw * c + y]), Rp[pw * c + x]);
-                            words += 2 * sp;
+                            if (STATS) words += 2 * sp;
                             if (STATS) { st_evals[1] += 1; st_wr += WRm; }
                             if (n >= kq) {
                                 if (STATS) st_passed[1] += 1;
@@ -1081,7 +1081,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (lane < got) {
                 x = XS(lv)[lane];
                 for (int pw = 0; pw < sp; ++pw) n += popc2(cr[pw], Rp[pw * c + x]);
-                words += 2 * sp;
+                if (STATS) words += 2 * sp;
             }
             const bool pass = lane < got && n >= kq;
             bool desc = false;
@@ -1089,7 +1089,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 const int lo = (x + 1) >> 5;
                 int m = 0;
                 for (int w = lo; w < WL; ++w) m += __popc(cl[w] & St[(int64_t)w * c + x]);
-                words += WL - lo;
+                if (STATS) words += WL - lo;
                 desc = m >= k - (ell + 1);
             }
             const unsigned dmb = __ballot_sync(kFull, desc);
@@ -1112,12 +1112,12 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         // the unit's sum goes to its job (and to its root when split by root)
         const u128 s = warp_sum_u128(unit_acc, ovf);
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
+        if (STATS) for (int o = 16; o >= 1; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
         if (lane == 0) {
             if (ovf) atomicOr(a.status, kStOverflow);
             atomic_add_u128(a.acc, s, a.status);
             if (a.per_root) atomic_add_u128(a.per_root + 2 * (int64_t)r, s, a.status);
-            atomicAdd(a.enum_words, words);
+            if (STATS) atomicAdd(a.enum_words, words);
         }
         ovf = false;
     }
