@@ -311,3 +311,13 @@ def test_root_ranges_add_up_to_the_count(gpu_ctx):
         assert parts[1] == oracle.count(g, p, q, anchor=anchor, roots=r)
         assert h.count_ex(p, q, anchor=anchor, roots=(0, n_a))[0] == h.count(p, q)
     h.close()
+
+
+@pytest.mark.parametrize("m,n,p,q,anchor", [(18, 18, 16, 2, "U"), (18, 18, 2, 16, "V"), (17, 17, 16, 16, "U"),
+                                            (17, 20, 16, 3, "U"), (20, 17, 3, 16, "V")])
+def test_deepest_search_trees(gpu_ctx, m, n, p, q, anchor):
+    """|L| = 16 on the anchor side: the enumeration runs at its largest depth
+    (13 levels below the level-2 units); complete graphs fix the count."""
+    h = gpu_ctx.load(bipgen.complete(m, n))
+    assert h.count_ex(p, q, anchor=anchor)[0] == math.comb(m, p) * math.comb(n, q)
+    h.close()
