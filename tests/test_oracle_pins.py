@@ -236,3 +236,25 @@ def test_golden_workload_values_and_generator_determinism():
     for key in ("2,2", "3,3", "1,3"):
         p, q = map(int, key.split(","))
         assert oracle.count(g, p, q) == int(fx["counts"][key])
+
+
+@pytest.mark.parametrize("m,n,p,q", [(9, 7, 3, 2), (12, 5, 4, 3), (10, 40, 5, 6), (8, 33, 4, 1), (14, 3, 6, 3)])
+def test_tree_statistics_closed_form_on_complete_graphs(m, n, p, q):
+    """The search-tree statistics (Alg. 1's nodes and the words a bitmap
+    implementation reads) in closed form on K_{m,n}.  All degrees are equal, so
+    the rank order is the id order; every pair shares n >= q neighbours, so
+    every evaluated child passes.  A node with |L| = s whose largest member is
+    i has C_L = the m - 1 - i later vertices and is entered when that is at
+    least p - s; the C(i, s - 1) nodes with largest member i each evaluate all
+    of their C_L.  C_R rows have ceil(n/32) words; C_L rows one word (m <= 33)."""
+    _, st = oracle.count(bipgen.complete(m, n), p, q, stats=True)
+    evals = [0] * len(st["evals"])
+    for s in range(1, p):
+        evals[s + 1] = sum(math.comb(i, s - 1) * (m - 1 - i) for i in range(m) if m - 1 - i >= p - s)
+    assert st["evals"] == evals
+    assert st["passed"] == evals
+    assert st["roots_expanded"] == max(0, m - p + 1)
+    wr = (n + 31) // 32
+    assert st["words_r"] == wr * sum(evals)
+    assert st["words_l"] == sum(evals[2:p])  # passed children that are not leaves, one word each
+    assert st["words_lvl2"] == wr * evals[2] + (evals[2] if p > 2 else 0)
