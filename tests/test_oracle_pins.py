@@ -258,3 +258,19 @@ def test_tree_statistics_closed_form_on_complete_graphs(m, n, p, q):
     assert st["words_r"] == wr * sum(evals)
     assert st["words_l"] == sum(evals[2:p])  # passed children that are not leaves, one word each
     assert st["words_lvl2"] == wr * evals[2] + (evals[2] if p > 2 else 0)
+
+
+@pytest.mark.parametrize("p,q", [(3, 2), (4, 3)])
+def test_tree_statistics_additive_over_disjoint_unions(p, q):
+    """Search trees never cross components (2-hop neighbours stay inside one),
+    and the rank order inside each component is kept, so every statistic of a
+    disjoint union is the sum of its parts'."""
+    g1 = bipgen.chung_lu(41, 200, 150, 1500, 2.1, 2.1)
+    g2 = bipgen.tiny_random(42, 20, 25, 0.4)
+    g3 = bipgen.complete(9, 11)
+    parts = [oracle.count(g, p, q, stats=True)[1] for g in (g1, g2, g3)]
+    _, whole = oracle.count(bipgen.disjoint_union(g1, g2, g3), p, q, stats=True)
+    for key in ("roots_expanded", "words_r", "words_l", "words_lvl2"):
+        assert whole[key] == sum(st[key] for st in parts), key
+    for key in ("evals", "passed"):
+        assert whole[key] == [sum(x) for x in zip(*(st[key] for st in parts))], key
