@@ -193,14 +193,17 @@ gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor,
  *   q: 1..GBC_MAX_PQ;  stream: a cudaStream_t passed as void* (NULL = the
  *     legacy default stream);  out: host, written on GBC_OK.
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call shares the array and it keeps the last
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture.  After
+ * cudaDeviceReset, or any other teardown of the device's primary context, the
+ * kept address is stale: do not call this entry point on that device again.  Every call shares the array and it keeps the last
  * call's contents (the call clears what must start at zero), so calls that
  * overlap on the GPU -- from other streams or threads -- race and give wrong
  * results: serialise them.
  * Errors: GBC_ERR_ARG; GBC_ERR_OOM when a vertex of U has more than
  * GBC_NOALLOC_MAX_2HOP higher-ranked (by (degree, id)) 2-hop neighbours, the
- * size its fixed scratch holds; GBC_ERR_OVERFLOW; GBC_ERR_CUDA.
+ * size its fixed scratch holds (the kernel stops at the first such vertex, so
+ * this error comes back quickly); GBC_ERR_OVERFLOW; GBC_ERR_CUDA.
  */
 gbc_status gbc_count_p2_noalloc(int32_t nU, int32_t nV, const int32_t *offU_d, const int32_t *adjU_d,
                                 const int32_t *offV_d, const int32_t *adjV_d, int q, void *stream,

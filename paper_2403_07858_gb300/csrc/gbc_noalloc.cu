@@ -62,20 +62,31 @@ k_p2_noalloc(int32_t nU, const int32_t *offU, const int32_t *adjU, const int32_t
     int32_t *vals = keys + kNaSlots;
     volatile int32_t *vkeys = keys, *vvals = vals;
     __shared__ int s_distinct;
+    __shared__ int s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr uint32_t mask = kNaSlots - 1;
+    const volatile int *vdistinct = &s_distinct;
     u128 sum = 0;
     bool ovf = false;
     for (int32_t u = blockIdx.x; u < nU; u += gridDim.x) {
         if (offU[u + 1] - offU[u] < q) continue;  // uniform: fewer than q neighbours
+        // once any root has overflowed the fixed table the call fails: skip the rest
+        if (threadIdx.x == 0) s_stop = (*(volatile uint32_t *)status & kNaTooLarge) != 0u;
         // the slab keeps the previous root's entries: clear it first
         for (int s = threadIdx.x; s < kNaSlots; s += blockDim.x) { keys[s] = -1; vals[s] = 0; }
         if (threadIdx.x == 0) s_distinct = 0;
         __syncthreads();
-        // wedges u - v - w with w ranked above u: a warp per v, lanes over N(v)
-        for (int32_t e = offU[u] + warp; e < offU[u + 1]; e += kNaThreads / 32) {
+        if (s_stop) break;  // block-uniform
+        // wedges u - v - w with w ranked above u: a warp per v, lanes over N(v).
+        // A thread stops as soon as the root has more distinct 2-hop neighbours
+        // than the table holds: at most GBC_NOALLOC_MAX_2HOP + kNaThreads keys
+        // are ever inserted, so every probe sequence finds a free slot within
+        // the table's 2 * GBC_NOALLOC_MAX_2HOP slots.
+        for (int32_t e = offU[u] + warp; e < offU[u + 1] && *vdistinct <= GBC_NOALLOC_MAX_2HOP;
+             e += kNaThreads / 32) {
             const int32_t v = adjU[e];
             for (int32_t f = offV[v] + lane; f < offV[v + 1]; f += 32) {
+                if (*vdistinct > GBC_NOALLOC_MAX_2HOP) break;
                 const int32_t w = adjV[f];
                 if (!above(offU, w, u)) continue;
                 uint32_t h = ((uint32_t)w * 2654435761u) & mask;
@@ -94,7 +105,7 @@ k_p2_noalloc(int32_t nU, const int32_t *offU, const int32_t *adjU, const int32_t
             }
         }
         __syncthreads();
-        if (*(volatile int *)&s_distinct <= GBC_NOALLOC_MAX_2HOP) {
+        if (*vdistinct <= GBC_NOALLOC_MAX_2HOP) {
             for (int s = threadIdx.x; s < kNaSlots; s += blockDim.x) {
                 const int32_t k = vkeys[s], cnt = vvals[s];
                 if (k >= 0 && cnt >= q) add_u128(sum, binom_exact(cnt, q, ovf), ovf);

@@ -1,7 +1,6 @@
 """Splitting one count across GPUs (or processes) by search-tree roots.
 
-The search trees of different roots are independent (Sec. III-B: "the search
-trees of distinct vertices are mutually independent"), so a count splits into
+Roots' search trees share nothing (Sec. III-B), so a count splits into
 disjoint root ranges with no exchange during the search; the only collective
 is one exact 128-bit sum at the end.  Host logic only: each rank counts its
 range with ``Graph.count_ex(..., roots=...)`` on its own GPU.
