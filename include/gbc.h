@@ -242,19 +242,50 @@ int gbc_tuned_anchor(gbc_graph_t g, int p, int q);
 
 /*
  * Serving (continuous batching).  gbc_serve_start starts `workers` threads
- * (0 = 2), each with its own CUDA streams and an equal share of the context's
- * scratch budget.  A free worker takes every waiting request, up to max_batch
- * (0 = 256), and runs them as one batched pipeline (gbc_count_batch's); requests
- * that arrive meanwhile wait for the next free worker, so successive batches
- * overlap on the device.  max_queue (0 = 4096) bounds the waiting requests;
- * time_limit_ms > 0 gives every request a device deadline (its poll then
- * returns GBC_ERR_TIMEOUT).  The paper has no serving layer; each served count
- * is the count of gbc_count.
+ * (0 = 4), each with its own CUDA streams.  Waiting requests are admitted by
+ * their scratch footprint (gbc_footprint): a free worker takes requests from
+ * the queue, up to max_batch (0 = 256), while their footprints fit in the part
+ * of the context's scratch budget that no running batch holds, and runs them
+ * as one batched pipeline (gbc_count_batch's).  Requests that arrive while
+ * others are on the GPU are admitted as workers and memory free up, so the
+ * pipelines of successive batches overlap on the device.  A request larger
+ * than the whole budget runs alone.  Each request completes as soon as its own
+ * count is done, not when its batch ends.  max_queue (0 = 4096) bounds the
+ * waiting requests; time_limit_ms > 0 gives every request a device deadline
+ * (its poll then returns GBC_ERR_TIMEOUT).  The paper has no serving layer;
+ * each served count is the count of gbc_count.
  */
 gbc_status gbc_serve_start(gbc_ctx_t ctx, int workers, int max_batch, int max_queue, int time_limit_ms);
 
 /* Stop serving: waiting requests are still run; results not yet polled are dropped. */
 gbc_status gbc_serve_stop(gbc_ctx_t ctx);
+
+/* Counters of the running server (host output of gbc_serve_stats_get). */
+typedef struct {
+    int64_t submitted;            /* requests accepted by gbc_submit */
+    int64_t rejected;             /* requests refused (queue full) */
+    int64_t admitted;             /* requests taken into a batch */
+    int64_t batches;              /* batches run */
+    int64_t peak_in_flight_bytes; /* most scratch reserved by running batches at once */
+    int64_t budget_bytes;         /* the scratch budget the batches share */
+    int32_t peak_running_batches; /* most batches on the device at once */
+    int32_t reserved_i;
+} gbc_serve_stats;
+
+/* The server's counters since gbc_serve_start.  Errors: GBC_ERR_ARG (null, not serving). */
+gbc_status gbc_serve_stats_get(gbc_ctx_t ctx, gbc_serve_stats *out);
+
+/*
+ * gbc_footprint -- device scratch bytes that the count of (g, p, q) holds (host
+ * output), the figure serving admission reserves for it.  *exact (host, may be
+ * NULL) is 1 when the same count already ran on this context and the figure is
+ * its measured scratch, 0 when it is an upper bound from load-time sums: root u
+ * keeps at most omega(u) / q' candidates (omega = its oriented wedges, q' the
+ * size on the other side), each with a C_R row of ceil(deg u / 32) words and a
+ * C_L row of at most |C_L| / 32 + 5 words (the truncated bitmaps of Sec. V-A
+ * sized per root).  Errors: GBC_ERR_ARG.
+ */
+gbc_status gbc_footprint(gbc_graph_t g, int p, int q, size_t *bytes, int *exact);
 
 /*
  * gbc_submit -- queue the count of (g, p, q) and return its ticket at once

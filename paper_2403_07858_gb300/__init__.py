@@ -18,6 +18,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -96,6 +97,16 @@ class CountInfo(ctypes.Structure):
         }
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("rejected", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("peak_in_flight_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("peak_running_batches", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved_i"}
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
@@ -124,6 +135,9 @@ SIGNATURES = {
     "gbc_tuned_anchor": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "gbc_serve_start": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gbc_serve_stop": (ctypes.c_int, [_vp]),
+    "gbc_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServeStats)]),
+    "gbc_footprint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_int)]),
     "gbc_submit": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gbc_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U128)]),
     "gbc_measure_int_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -189,6 +203,7 @@ class Graph:
     def __init__(self, ctx: "Context", handle: int):
         self._ctx = ctx
         self._h = ctypes.c_void_p(handle)
+        ctx._graphs.add(self)
         n_u, n_v, mu, mv = _i32(), _i32(), _i32(), _i32()
         n_e = _i64()
         _check(load_library().gbc_graph_info(self._h, ctypes.byref(n_u), ctypes.byref(n_v), ctypes.byref(n_e),
@@ -229,6 +244,13 @@ class Graph:
                                            ctypes.byref(info)), "gbc_count_ex")
         return out.value(), info.as_dict()
 
+    def footprint(self, p: int, q: int) -> tuple[int, bool]:
+        """Scratch bytes the (p,q) count holds: (bytes, exact); exact once the
+        same count ran on this context, else a load-time upper bound."""
+        b, e = ctypes.c_size_t(), ctypes.c_int()
+        _check(load_library().gbc_footprint(self._h, p, q, ctypes.byref(b), ctypes.byref(e)), "gbc_footprint")
+        return int(b.value), bool(e.value)
+
     def tuned_anchor(self, p: int, q: int) -> str | None:
         return _ANCHOR_NAMES.get(load_library().gbc_tuned_anchor(self._h, p, q))
 
@@ -250,6 +272,7 @@ class Context:
         _check(lib.gbc_ctx_create(device, mem_budget_bytes, ctypes.byref(h)), "gbc_ctx_create")
         self._h = h
         self.device = device
+        self._graphs = weakref.WeakSet()  # graphs still loaded, freed before the context
 
     def set_stream(self, stream) -> None:
         """Run later calls on ``stream`` (a torch.cuda.Stream, a raw handle, or None)."""
@@ -257,8 +280,13 @@ class Context:
         _check(load_library().gbc_ctx_set_stream(self._h, ctypes.c_void_p(handle or 0)), "gbc_ctx_set_stream")
 
     def close(self):
+        """Stop serving, free the graphs still loaded on this context, then the context."""
         if self._h:
-            load_library().gbc_ctx_destroy(self._h)
+            lib = load_library()
+            lib.gbc_serve_stop(self._h)
+            for g in list(self._graphs):
+                g.close()
+            lib.gbc_ctx_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def load_graph(self, n_u: int, n_v: int, off_u, adj_u, off_v, adj_v) -> Graph:
@@ -307,6 +335,11 @@ class Context:
 
     def serve_stop(self):
         _check(load_library().gbc_serve_stop(self._h), "gbc_serve_stop")
+
+    def serve_stats(self) -> dict:
+        st = ServeStats()
+        _check(load_library().gbc_serve_stats_get(self._h, ctypes.byref(st)), "gbc_serve_stats_get")
+        return st.as_dict()
 
     def submit(self, graph: "Graph", p: int, q: int) -> int:
         t = ctypes.c_uint64()

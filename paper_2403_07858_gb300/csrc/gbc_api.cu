@@ -9,6 +9,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -58,6 +59,26 @@ struct Lane {
     cudaStream_t st = nullptr;
     cudaStream_t aux[kAuxStreams] = {};      // per-job launches of a batch overlap on these
     cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
+    DoneRec *done_h = nullptr;               // host-mapped completion records of a batch
+    DoneRec *done_d = nullptr;               // the same records as device pointers
+    int done_cap = 0;
+    // Completion records for n counts, zeroed (grows the mapped buffer as needed).
+    cudaError_t ensure_done(int n) {
+        if (n > done_cap) {
+            if (done_h) cudaFreeHost(done_h);
+            done_h = nullptr;
+            done_cap = 0;
+            const int cap = std::max(n, 64);
+            cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&done_h), sizeof(DoneRec) * cap,
+                                          cudaHostAllocMapped);
+            if (e != cudaSuccess) { done_h = nullptr; return e; }
+            e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&done_d), done_h, 0);
+            if (e != cudaSuccess) return e;
+            done_cap = cap;
+        }
+        memset(done_h, 0, sizeof(DoneRec) * n);
+        return cudaSuccess;
+    }
     cudaError_t create(cudaStream_t main) {
         st = main;
         cudaError_t e = cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
@@ -73,6 +94,21 @@ struct Lane {
             if (join_ev[i]) cudaEventDestroy(join_ev[i]);
         }
         if (fork_ev) cudaEventDestroy(fork_ev);
+        if (done_h) cudaFreeHost(done_h);
+        done_h = nullptr;
+        done_cap = 0;
+    }
+};
+
+// Exact scratch footprint of a count, keyed by (graph, anchor, |L|, |R|),
+// remembered after the count first runs (serving admission).
+struct FootKey {
+    const void *graph;
+    int anchor, k, kq;
+    bool operator<(const FootKey &o) const {
+        if (graph != o.graph) return graph < o.graph;
+        if (anchor != o.anchor) return anchor < o.anchor;
+        return k != o.k ? k < o.k : kq < o.kq;
     }
 };
 
@@ -86,6 +122,7 @@ struct gbc_ctx_s {
     Lane lane;                               // the lane of the synchronous calls
     std::mutex tune_mu;
     std::map<TuneKey, int> tuned_anchor;     // filled by gbc_autotune
+    std::map<FootKey, size_t> footprint;     // exact scratch bytes of counts that ran (tune_mu)
     std::mutex mu;
     int live_graphs = 0;
     Server *server = nullptr;                // gbc_submit / gbc_poll
@@ -106,6 +143,10 @@ struct gbc_graph_s {
     int32_t binom_nmax = 0;
     int32_t *callerU = nullptr, *callerV = nullptr;  // caller's id of every (renumbered) vertex
     std::vector<int32_t> callerU_h, callerV_h;
+    // per anchor side (0: U, 1: V): sum omega, sum omega * row_stride(deg),
+    // max omega, roots with omega > 0, sum omega^2 (double bits); omega(u) =
+    // oriented wedges of root u.  They bound a count's scratch before it runs.
+    unsigned long long fp[2][5] = {};
 };
 
 // Stream-ordered scratch that is released when the owner goes out of scope.
@@ -204,6 +245,8 @@ void gbc_free_graph(gbc_graph_t g) {
         std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
         for (auto it = g->ctx->tuned_anchor.begin(); it != g->ctx->tuned_anchor.end();)
             it = it->first.graph == g ? g->ctx->tuned_anchor.erase(it) : std::next(it);
+        for (auto it = g->ctx->footprint.begin(); it != g->ctx->footprint.end();)
+            it = it->first.graph == g ? g->ctx->footprint.erase(it) : std::next(it);
     }
     delete g;
 }
@@ -429,6 +472,16 @@ static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32
     }
     CKG(launch_mirror(g->offU, g->adjU, nU, g->offV, g->adjV_byU, g->degU, g->mirrorU, st));
     CKG(launch_mirror(g->offV, g->adjV, nV, g->offU, g->adjU_byV, g->degV, g->mirrorV, st));
+    {
+        unsigned long long *d_fp = nullptr;
+        CKG(cudaMallocAsync((void **)&d_fp, sizeof(g->fp), st));
+        CKG(cudaMemsetAsync(d_fp, 0, sizeof(g->fp), st));
+        CKG(launch_footprint_sums(g->offU, nU, g->adjU, g->offV, g->mirrorU, d_fp, st));
+        CKG(launch_footprint_sums(g->offV, nV, g->adjV, g->offU, g->mirrorV, d_fp + 5, st));
+        CKG(cudaMemcpyAsync(g->fp, d_fp, sizeof(g->fp), cudaMemcpyDeviceToHost, st));
+        CKG(cudaStreamSynchronize(st));
+        cudaFreeAsync(d_fp, st);
+    }
     // binomial table up to the largest degree (|C_R| never exceeds it)
     g->binom_nmax = std::max(std::max(g->maxdegU, g->maxdegV), 1);
     CKG(cudaMallocAsync((void **)&g->binom, (size_t)(g->binom_nmax + 1) * (kMaxPQ + 1) * sizeof(ulonglong2), st));
@@ -506,6 +559,7 @@ struct Small {
     int32_t cand_max;
     unsigned long long deadline;
     unsigned long long enum_words;
+    int32_t fin[2];   // completion counters (DoneRec publishing)
 };
 
 // One count of a (possibly one-element) batch.
@@ -518,6 +572,7 @@ struct Job {
     Small h;
     bool trivial = false;
     size_t scratch_bytes = 0;  // device scratch held while this job ran
+    size_t base_bytes = 0;     // scratch of the root classification and scans (before the waves)
     gbc_status st = GBC_OK;
     char err[256] = "";
     void set_error(gbc_status s, const char *fmt, ...) {
@@ -529,20 +584,117 @@ struct Job {
     }
 };
 
+// Scratch bytes a count of (g, p, q) from `anchor` holds: the exact figure if
+// the same count ran before on this context (*exact = 1), else an upper bound
+// from the load-time wedge sums (*exact = 0).  Root u keeps at most
+// c <= omega(u) / kq candidates (each needs kq wedges), with R rows of
+// row_stride(d) words each; for |L| >= 4 its S and T blocks take
+// (c + 32 row_stride(d)) ceil(c / 32) words, at most
+// c^2 / 32 + 3c + c row_stride(d) + d + 64.
+static size_t footprint_of(const gbc_graph_s *g, int anchor, int p, int q, int *exact) {
+    const int k = anchor == GBC_ANCHOR_U ? p : q, kq = anchor == GBC_ANCHOR_U ? q : p;
+    {
+        std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
+        auto it = g->ctx->footprint.find(FootKey{g, anchor, k, kq});
+        if (it != g->ctx->footprint.end()) {
+            if (exact) *exact = 1;
+            return it->second;
+        }
+    }
+    if (exact) *exact = 0;
+    const int side = anchor == GBC_ANCHOR_U ? 0 : 1;
+    const int64_t nA = side == 0 ? g->nU : g->nV;
+    const unsigned long long *f = g->fp[side];
+    double sq;
+    memcpy(&sq, &f[4], sizeof sq);
+    const double so = (double)f[0], sos = (double)f[1], omax = (double)f[2], npos = (double)f[3];
+    double base = (double)sizeof(Small) + 20.0 * nA + 24.0 * (nA + 1) + 24.0 * ((nA + 1) / 2048 + 2);
+    if (k >= 2 && omax > kCtaTierOmega) {  // global-table tier: one hash slab per CTA
+        double slots = 32, sortcap = 1;
+        while (slots < 2 * omax) slots *= 2;
+        while (sortcap < omax) sortcap *= 2;
+        base += 4.0 * (2 * slots + 2 * sortcap) * std::min(2.0 * g->ctx->n_sms, std::max(npos, 1.0));
+    }
+    if (k <= 2) return (size_t)base;
+    const double c = so / kq, r = sos / kq;
+    const double sw = k >= 4 ? sq / (32.0 * kq * (double)kq) + 3.0 * c + r + (double)g->nE + 64.0 * npos : 0.0;
+    const double need = 12.0 * c + 4.0 * r + 4.0 * sw + 8.0 * (double)std::max<int64_t>(g->nE, 1) +
+                        (k >= 4 ? 17.0 * c : 0.0);
+    const double tot = base + need;
+    return tot >= 1.8e19 ? (size_t)-1 : (size_t)tot;
+}
+
+// Outcome of job i of a batch, handed over as soon as it is known.
+typedef std::function<void(int, gbc_status, gbc_u128, const char *)> DoneFn;
+
+// Status of a job from its device status word (the job's own error first).
+static gbc_status classify(const Job &J, uint32_t status, char *msg, size_t n) {
+    if (J.st != GBC_OK) { snprintf(msg, n, "%s", J.err); return J.st; }
+    if (status & kStTimeout) { snprintf(msg, n, "gbc_count: (%d,%d) passed its time limit", J.p, J.q); return GBC_ERR_TIMEOUT; }
+    if (status & kStOverflow) { snprintf(msg, n, "gbc_count: (%d,%d) count exceeds 2^128-1", J.p, J.q); return GBC_ERR_OVERFLOW; }
+    if (status) { snprintf(msg, n, "gbc_count: device status 0x%x", status); return GBC_ERR_CUDA; }
+    msg[0] = 0;
+    return GBC_OK;
+}
+
+// Scratch bytes of the wave phase of a job with |L| = k, from its per-root
+// scan totals (candidates, R words, S words) and |E|: candidate ids and roots,
+// per-edge position counts and maps, the R and S(+T) blocks, and for k >= 4
+// the unit lists.
+static size_t wave_need(int k, const int64_t totals[3], int64_t nE) {
+    size_t b = (size_t)totals[0] * 8 + (size_t)std::max<int64_t>(totals[1], 1) * 4 +
+               (size_t)std::max<int64_t>(nE, 1) * 8;
+    if (k >= 4) b += (size_t)std::max<int64_t>(totals[2], 1) * 4 + (size_t)totals[0] * 17 + sizeof(CountArgs) + 256;
+    return b;
+}
+
 // Runs every job of the batch phase by phase on the context's stream: one host
 // synchronisation after the root classification, one after the per-root
 // scans, and one at the end, whatever the number of jobs.  The enumeration of
 // all jobs with |L| >= 4 is one persistent launch (a job table on the device).
 // Per-job scratch is granted in waves that fit the context's budget.
+// on_done (optional): called for each job as soon as its outcome is known --
+// jobs that end early (trivial, |L| <= 2, no candidates) at the host
+// synchronisations, the others when their last kernel work is done, which the
+// device reports through host-mapped completion records while the rest of the
+// batch is still running.
 // Returns a batch-level error (CUDA failure); per-job outcomes are in job.st.
 static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vector<Job> &jobs,
-                           const gbc_count_options *opt, bool want_stats, Timer &tm, SearchStats *hs_out) {
+                           const gbc_count_options *opt, bool want_stats, Timer &tm, SearchStats *hs_out,
+                           const DoneFn *on_done = nullptr) {
     cudaStream_t st = lane.st;
     const int n = (int)jobs.size();
     Scratch sc(st);
     Small *d_small = nullptr;
     CK(sc.get(&d_small, n));
     CK(cudaMemsetAsync(d_small, 0, sizeof(Small) * n, st));
+    if (on_done) CK(lane.ensure_done(n));
+    std::vector<char> released(n, 0);
+    auto release = [&](int i, const unsigned long long *acc, uint32_t status) {
+        if (!on_done || released[i]) return;
+        released[i] = 1;
+        char msg[256];
+        const gbc_status s = classify(jobs[i], status, msg, sizeof msg);
+        (*on_done)(i, s, gbc_u128{acc[0], acc[1]}, msg);
+    };
+    // Waits for the stream, handing over the jobs of `ids` whose completion
+    // records the device has published meanwhile.
+    auto wait_releasing = [&](const std::vector<int> &ids) -> cudaError_t {
+        while (true) {
+            const cudaError_t q = cudaStreamQuery(st);
+            for (int i : ids) {
+                if (released[i]) continue;
+                DoneRec *d = lane.done_h + i;
+                if (__atomic_load_n(&d->flag, __ATOMIC_ACQUIRE)) {
+                    const volatile DoneRec *vd = d;
+                    const unsigned long long acc[2] = {vd->acc[0], vd->acc[1]};
+                    release(i, acc, vd->status);
+                }
+            }
+            if (q != cudaErrorNotReady) return q;
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+        }
+    };
     SearchStats *d_stats = nullptr;
     if (want_stats) {
         CK(sc.get(&d_stats, 1));
@@ -595,6 +747,8 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             a.root_end = std::min(a.g.nA, opt->root_end);
         }
         Small *s = d_small + i;
+        a.fin = s->fin;
+        a.done = on_done ? lane.done_d + i : nullptr;
         a.acc = s->acc;
         a.status = &s->status;
         a.tier_count = s->tier_count;
@@ -619,9 +773,11 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     for (Job &J : jobs) {
         if (!active(J)) continue;
         const int64_t nA = J.a.g.nA;
+        const size_t b0 = sc.bytes;
         CK(sc.get(&J.a.omega, nA));
         CK(sc.get(&J.a.tier_list, 3 * nA));
         CK(sc.get(&J.a.cand_count, nA));
+        J.base_bytes += sc.bytes - b0 + sizeof(Small);
         any = true;
     }
     CK(fork());
@@ -631,6 +787,8 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     if (any) {
         CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i)  // trivial and single-vertex jobs are complete
+            if (!active(jobs[i])) release(i, hs[i].acc, hs[i].status);
     }
     // ---- phase 2: candidates (pass A) and, for |L| >= 3, the per-root offsets
     any = false;
@@ -640,6 +798,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         if (!active(J)) continue;
         CountArgs &a = J.a;
         const Small &h = hs[i];
+        const size_t b0 = sc.bytes;
         if (h.tier_count[2] > 0) {
             if (h.omega_max[2] > (1 << 28)) {
                 J.set_error(GBC_ERR_OOM, "gbc_count: a root has %d oriented wedges (limit 2^28)", h.omega_max[2]);
@@ -664,6 +823,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             a.s_off = s_off;
             any = true;
         }
+        J.base_bytes += sc.bytes - b0;
     }
     CK(fork());
     for (int i = 0; i < n; ++i) {
@@ -677,6 +837,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     }
     CK(join());
     tm.mark(1, st);
+    const bool sized = any;  // the scan totals of every |L| >= 3 job are on the host
     if (any) {
         CK(cudaMemcpyAsync(hs.data(), d_small, sizeof(Small) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -694,12 +855,19 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         }
         todo.push_back(i);
     }
-    auto need_of = [&](int i) {
-        const Small &h = hs[i];
-        const Job &J = jobs[i];
-        return (size_t)h.totals[0] * 12 + (size_t)h.totals[1] * 4 + (size_t)h.totals[2] * 4 +
-               (size_t)std::max<int64_t>(J.g->nE, 1) * 8;
-    };
+    auto need_of = [&](int i) { return wave_need(jobs[i].a.k, hs[i].totals, jobs[i].g->nE); };
+    std::vector<char> in_todo(n, 0);
+    for (int i : todo) in_todo[i] = 1;
+    // exact footprint of each job that got through the scans (serving admission)
+    std::vector<size_t> foot(n, 0);
+    for (int i = 0; i < n; ++i)
+        if (active(jobs[i]) && jobs[i].st == GBC_OK) foot[i] = jobs[i].base_bytes + (in_todo[i] ? need_of(i) : 0);
+    if (sized) {
+        // everything not waiting for the waves is complete (|L| = 2 summed its
+        // leaves in pass A; no candidates means a zero count)
+        for (int i = 0; i < n; ++i)
+            if (!in_todo[i]) release(i, hs[i].acc, hs[i].status);
+    }
     size_t pos = 0;
     while (pos < todo.size()) {
         Scratch wave_sc(st);
@@ -712,6 +880,8 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                 if (wave.empty()) {
                     jobs[i].set_error(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need,
                                       budget);
+                    const unsigned long long zero[2] = {0, 0};
+                    release(i, zero, 0);
                     continue;
                 }
                 break;
@@ -785,7 +955,10 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, want_stats, opt ? opt->enum_warps : 0,
                                 max_wr, max_wl, max_k, ctx->n_sms, st));
             // the job table is read by the launch: keep the host copy alive until it has run
-            CK(cudaStreamSynchronize(st));
+            if (on_done) CK(wait_releasing(wave));
+            else CK(cudaStreamSynchronize(st));
+        } else if (on_done) {
+            CK(wait_releasing(wave));  // |L| = 3 counts publish from the pairwise kernel
         }
         for (int i : wave) jobs[i].scratch_bytes = sc.bytes + wave_sc.bytes;
     }
@@ -796,16 +969,19 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     if (d_stats && hs_out) CK(cudaMemcpyAsync(hs_out, d_stats, sizeof(SearchStats), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(cudaGetLastError());
+    if (!(opt && opt->root_end > opt->root_begin)) {  // remember full counts' footprints
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        for (int i = 0; i < n; ++i)
+            if (foot[i]) ctx->footprint[FootKey{jobs[i].g, jobs[i].anchor, jobs[i].a.k, jobs[i].a.kq}] = foot[i];
+    }
     for (int i = 0; i < n; ++i) {
         Job &J = jobs[i];
         J.h = hs[i];
+        release(i, J.h.acc, J.h.status);
         if (J.st != GBC_OK) continue;
-        if (J.h.status & kStTimeout)
-            J.set_error(GBC_ERR_TIMEOUT, "gbc_count: (%d,%d) passed its time limit", J.p, J.q);
-        else if (J.h.status & kStOverflow)
-            J.set_error(GBC_ERR_OVERFLOW, "gbc_count: (%d,%d) count exceeds 2^128-1", J.p, J.q);
-        else if (J.h.status)
-            J.set_error(GBC_ERR_CUDA, "gbc_count: device status 0x%x", J.h.status);
+        char msg[256];
+        const gbc_status s = classify(J, J.h.status, msg, sizeof msg);
+        if (s != GBC_OK) J.set_error(s, "%s", msg);
     }
     return GBC_OK;
 }
@@ -1002,17 +1178,28 @@ extern "C" int gbc_tuned_anchor(gbc_graph_t g, int p, int q) {
 }
 
 // ---------------------------------------------------------------------------
-// Serving: gbc_submit / gbc_poll.  Worker threads, each with its own lane of
-// streams and an equal share of the context's scratch budget, take every
-// request waiting when they become free (up to max_batch) and run them as one
-// batched pipeline.  Requests that arrive while batches are on the GPU wait for
-// the next free worker, so with several workers the pipelines of successive
-// batches overlap on the device (continuous batching).  Admission refuses a
-// request when max_queue requests are already waiting.
+// Serving: gbc_submit / gbc_poll (continuous batching).
+//
+// Requests wait in a FIFO queue.  Each worker thread has its own lane of
+// streams; a free worker takes waiting requests as one batch while their
+// scratch footprints (footprint_of: exact once the same count has run, else an
+// upper bound from the graph's wedge sums) fit in the part of the context's
+// budget that no other batch holds.  A request that fits nowhere waits until
+// running batches give memory back; one that exceeds the whole budget runs
+// alone.  The head of the queue is passed over by smaller requests at most
+// kMaxSkips times, so it is never starved.  Every request is released as soon
+// as its own count is done -- counts that finish early in the pipeline at the
+// host synchronisations, the others through the device's completion records --
+// not when the whole batch ends, and its memory returns when the batch ends.
+// Submission refuses a request when max_queue requests are already waiting.
+constexpr int kMaxSkips = 16;
+
 struct Request {
     uint64_t ticket = 0;
     gbc_graph_s *g = nullptr;
     int p = 0, q = 0, time_limit_ms = 0;
+    size_t foot = 0;        // scratch bytes reserved for it (footprint_of)
+    int skipped = 0;        // times a later request was admitted ahead of it
     bool done = false;
     gbc_status st = GBC_OK;
     gbc_u128 val{0, 0};
@@ -1027,24 +1214,60 @@ struct Server {
     uint64_t next_ticket = 1;
     bool stop = false;
     int max_batch = 256, max_queue = 4096, time_limit_ms = 0;
-    size_t budget_per_worker = 0;
+    size_t budget = 0;          // scratch budget shared by the workers' batches
+    size_t in_flight = 0;       // scratch reserved by the batches on the device
+    gbc_serve_stats stats{};
+    int running = 0;            // batches on the device
     std::vector<std::thread> threads;
     std::vector<Lane> lanes;
     std::vector<cudaStream_t> own_streams;
 };
 
+// Takes the next batch for a worker (caller holds sv->mu); empty if nothing fits.
+static std::vector<Request *> take_batch(Server *sv, size_t &reserved) {
+    std::vector<Request *> batch;
+    reserved = 0;
+    for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)batch.size() < sv->max_batch;) {
+        Request *r = *it;
+        const bool alone = sv->in_flight == 0 && batch.empty();
+        const bool fits = sv->in_flight + reserved + r->foot <= sv->budget;
+        if (alone || fits) {
+            batch.push_back(r);
+            reserved += std::min(r->foot, sv->budget);  // alone, it may use the whole budget and no more
+            it = sv->pending.erase(it);
+            continue;
+        }
+        if (it == sv->pending.begin()) {
+            // the head does not fit: later requests may pass it a bounded number of times
+            if (++r->skipped > kMaxSkips) break;
+        }
+        ++it;
+    }
+    return batch;
+}
+
 static void serve_loop(gbc_ctx_s *ctx, Server *sv, int w) {
     cudaSetDevice(ctx->device);
     while (true) {
         std::vector<Request *> batch;
+        size_t reserved = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
-            if (sv->pending.empty()) return;  // stopping and drained
-            while (!sv->pending.empty() && (int)batch.size() < sv->max_batch) {
-                batch.push_back(sv->pending.front());
-                sv->pending.pop_front();
+            while (true) {
+                if (sv->pending.empty()) {
+                    if (sv->stop) return;  // stopping and drained
+                } else {
+                    batch = take_batch(sv, reserved);
+                    if (!batch.empty()) break;
+                }
+                sv->cv_work.wait(lk);
             }
+            sv->in_flight += reserved;
+            sv->running += 1;
+            sv->stats.batches += 1;
+            sv->stats.admitted += (int64_t)batch.size();
+            sv->stats.peak_in_flight_bytes = std::max<int64_t>(sv->stats.peak_in_flight_bytes, (int64_t)sv->in_flight);
+            sv->stats.peak_running_batches = std::max<int32_t>(sv->stats.peak_running_batches, sv->running);
         }
         std::vector<Job> jobs(batch.size());
         for (size_t i = 0; i < batch.size(); ++i) {
@@ -1054,24 +1277,36 @@ static void serve_loop(gbc_ctx_s *ctx, Server *sv, int w) {
             jobs[i].time_limit_ms = batch[i]->time_limit_ms;
             jobs[i].anchor = resolve_anchor(batch[i]->g, batch[i]->p, batch[i]->q, 0);
         }
+        // finished[i]: request i was handed over (a poll may have freed it since)
+        std::vector<char> finished(batch.size(), 0);
+        const DoneFn on_done = [&](int i, gbc_status st, gbc_u128 v, const char *msg) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            finished[i] = 1;
+            Request *r = batch[i];
+            r->st = st;
+            r->val = v;
+            snprintf(r->err, sizeof r->err, "%s", msg);
+            r->done = true;
+            sv->cv_done.notify_all();
+        };
         Timer tm;
         tm.init(false);
-        const gbc_status s = run_jobs(ctx, sv->lanes[w], sv->budget_per_worker, jobs, nullptr, false, tm, nullptr);
+        // a batch may use what it reserved (a request too large for any share runs alone on the whole budget)
+        const size_t run_budget = reserved;
+        const gbc_status s = run_jobs(ctx, sv->lanes[w], run_budget, jobs, nullptr, false, tm, nullptr, &on_done);
         const char *batch_err = s == GBC_OK ? "" : gbc_last_error();
         std::lock_guard<std::mutex> lk(sv->mu);
         for (size_t i = 0; i < batch.size(); ++i) {
+            if (finished[i]) continue;
             Request *r = batch[i];
-            if (s != GBC_OK) {
-                r->st = s;
-                snprintf(r->err, sizeof r->err, "%s", batch_err);
-            } else {
-                r->st = jobs[i].st;
-                snprintf(r->err, sizeof r->err, "%s", jobs[i].err);
-                if (jobs[i].st == GBC_OK) r->val = gbc_u128{jobs[i].h.acc[0], jobs[i].h.acc[1]};
-            }
+            r->st = s != GBC_OK ? s : GBC_ERR_CUDA;
+            snprintf(r->err, sizeof r->err, "%s", s != GBC_OK ? batch_err : "gbc_serve: request not completed");
             r->done = true;
         }
+        sv->in_flight -= reserved;
+        sv->running -= 1;
         sv->cv_done.notify_all();
+        sv->cv_work.notify_all();  // memory came back: waiting requests may fit now
     }
 }
 
@@ -1098,11 +1333,11 @@ extern "C" gbc_status gbc_serve_start(gbc_ctx_t ctx, int workers, int max_batch,
     if (ctx->server) return fail(GBC_ERR_ARG, "gbc_serve_start: already serving");
     CK(cudaSetDevice(ctx->device));
     Server *sv = new Server();
-    const int nw = workers ? workers : 2;
+    const int nw = workers ? workers : 4;
     sv->max_batch = max_batch ? max_batch : 256;
     sv->max_queue = max_queue ? max_queue : 4096;
     sv->time_limit_ms = time_limit_ms;
-    sv->budget_per_worker = ctx->budget / (size_t)nw;
+    sv->budget = ctx->budget;
     sv->lanes.resize(nw);
     for (int w = 0; w < nw; ++w) {
         cudaStream_t s = nullptr;
@@ -1127,6 +1362,24 @@ extern "C" gbc_status gbc_serve_stop(gbc_ctx_t ctx) {
     return GBC_OK;
 }
 
+extern "C" gbc_status gbc_serve_stats_get(gbc_ctx_t ctx, gbc_serve_stats *out) {
+    if (!ctx || !out) return fail(GBC_ERR_ARG, "gbc_serve_stats_get: null argument");
+    Server *sv = ctx->server;
+    if (!sv) return fail(GBC_ERR_ARG, "gbc_serve_stats_get: not serving");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->budget_bytes = (int64_t)sv->budget;
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_footprint(gbc_graph_t g, int p, int q, size_t *bytes, int *exact) {
+    if (!g || !bytes) return fail(GBC_ERR_ARG, "gbc_footprint: null argument");
+    if (p < 1 || q < 1 || p > GBC_MAX_PQ || q > GBC_MAX_PQ)
+        return fail(GBC_ERR_ARG, "gbc_footprint: p=%d q=%d outside [1, %d]", p, q, GBC_MAX_PQ);
+    *bytes = footprint_of(g, resolve_anchor(g, p, q, 0), p, q, exact);
+    return GBC_OK;
+}
+
 extern "C" gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uint64_t *ticket) {
     if (!ctx || !g || !ticket || g->ctx != ctx) return fail(GBC_ERR_ARG, "gbc_submit: bad argument");
     if (p < 1 || q < 1 || p > GBC_MAX_PQ || q > GBC_MAX_PQ)
@@ -1136,17 +1389,22 @@ extern "C" gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uin
         if (s != GBC_OK && !ctx->server) return s;
     }
     Server *sv = ctx->server;
+    const size_t foot = footprint_of(g, resolve_anchor(g, p, q, 0), p, q, nullptr);
     std::lock_guard<std::mutex> lk(sv->mu);
-    if ((int)sv->pending.size() >= sv->max_queue)
+    if ((int)sv->pending.size() >= sv->max_queue) {
+        sv->stats.rejected += 1;
         return fail(GBC_ERR_REJECTED, "gbc_submit: %d requests already waiting", (int)sv->pending.size());
+    }
     Request *r = new Request();
     r->ticket = sv->next_ticket++;
     r->g = g;
     r->p = p;
     r->q = q;
     r->time_limit_ms = sv->time_limit_ms;
+    r->foot = foot;
     sv->all[r->ticket] = r;
     sv->pending.push_back(r);
+    sv->stats.submitted += 1;
     *ticket = r->ticket;
     sv->cv_work.notify_one();
     return GBC_OK;

@@ -159,6 +159,15 @@ void set_last_error(const char *msg);
 // the calling thread, serialised per context).
 extern thread_local int t_launches;
 
+// Completion record of one count in host-mapped memory: the device writes the
+// result and then sets flag, so a waiting host thread can release the count as
+// soon as its last kernel work is done, before the rest of its batch finishes.
+struct DoneRec {
+    unsigned long long acc[2];
+    uint32_t status;
+    uint32_t flag;
+};
+
 // Everything one count's kernels share (device pointers).
 struct CountArgs {
     SideView g;
@@ -202,7 +211,22 @@ struct CountArgs {
     unsigned long long *enum_words; // [1] C_R + C_L words read by the enumeration kernel
     int32_t *poscnt;                // [|E|] per anchor edge slot: candidates containing that position
     int32_t *posmap;                // [|E|] per anchor edge slot: its bit position in the R rows
+    DoneRec *done;                  // host-mapped completion record, or null (no early release)
+    int32_t *fin;                   // [2] exited k_pairs warps, finished enumeration units
 };
+
+// Writes the count's final sum and status to its completion record (called by
+// the one thread that finishes the count's last piece of work, after a fence).
+__device__ __forceinline__ void publish_done(const CountArgs &a) {
+    volatile DoneRec *d = a.done;
+    const unsigned long long lo = atomicAdd(a.acc, 0ull), hi = atomicAdd(a.acc + 1, 0ull);
+    const uint32_t st = atomicOr(a.status, 0u);
+    d->acc[0] = lo;
+    d->acc[1] = hi;
+    d->status = st;
+    __threadfence_system();
+    d->flag = 1u;
+}
 
 // R rows of a root with d neighbours take ceil(d/32) words, stored with an even
 // stride so that two words load at once.
@@ -250,6 +274,10 @@ cudaError_t launch_rank_sort_rows(const int32_t *off, const int32_t *adj, int32_
 cudaError_t launch_mirror(const int32_t *offA, const int32_t *adjA, int32_t nA, const int32_t *offO,
                           const int32_t *adjO_rank, const int32_t *degA, int32_t *mirror, cudaStream_t st);
 cudaError_t launch_binomial(ulonglong2 *c, int32_t *n_ovf, int32_t nmax, cudaStream_t st);
+// out[5] (zeroed): sum omega, sum omega * row_stride(deg), max omega, roots with
+// omega > 0, sum omega^2 (double bits) over the anchor side A.
+cudaError_t launch_footprint_sums(const int32_t *offA, int32_t nA, const int32_t *adjA, const int32_t *offO,
+                                  const int32_t *mirror, unsigned long long *out, cudaStream_t st);
 
 cudaError_t launch_single_vertex_sets(const CountArgs &a, cudaStream_t st);
 cudaError_t launch_set_deadline(unsigned long long *deadline, unsigned long long limit_ns, cudaStream_t st);

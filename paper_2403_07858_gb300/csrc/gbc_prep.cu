@@ -234,6 +234,54 @@ __global__ void k_fill_i32(int32_t *p, int32_t n, int32_t v) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
+// ---------------------------------------------------------------------------
+// Per-side sums behind the scratch-footprint bound of a count (serving
+// admission): with omega(u) the oriented wedges of root u (wedges u - o - w
+// with w ranked above u), a root keeps at most omega(u) / kq candidates, each
+// with an R row of row_stride(deg u) words and an S row of about c / 32 words.
+// out: [0] sum omega, [1] sum omega * row_stride(deg), [2] max omega,
+// [3] roots with omega > 0, [4] sum omega^2 (as the bits of a double).
+__global__ void k_footprint_sums(const int32_t *offA, int32_t nA, const int32_t *adjA, const int32_t *offO,
+                                 const int32_t *mirror, unsigned long long *out) {
+    unsigned long long s0 = 0, s1 = 0, mx = 0, npos = 0;
+    double sq = 0.0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nA; u += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long om = 0;
+        for (int32_t e = offA[u]; e < offA[u + 1]; ++e) {
+            const int32_t o = adjA[e];
+            om += (unsigned long long)(offO[o + 1] - offO[o] - mirror[e] - 1);
+        }
+        s0 += om;
+        s1 += om * (unsigned long long)row_stride(offA[u + 1] - offA[u]);
+        mx = om > mx ? om : mx;
+        npos += om > 0;
+        sq += (double)om * (double)om;
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        s0 += __shfl_xor_sync(kFull, s0, o);
+        s1 += __shfl_xor_sync(kFull, s1, o);
+        const unsigned long long m2 = __shfl_xor_sync(kFull, mx, o);
+        mx = m2 > mx ? m2 : mx;
+        npos += __shfl_xor_sync(kFull, npos, o);
+        sq += __shfl_xor_sync(kFull, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], s0);
+        atomicAdd(&out[1], s1);
+        atomicMax(&out[2], mx);
+        atomicAdd(&out[3], npos);
+        atomicAdd(reinterpret_cast<double *>(&out[4]), sq);
+    }
+}
+
+cudaError_t launch_footprint_sums(const int32_t *offA, int32_t nA, const int32_t *adjA, const int32_t *offO,
+                                  const int32_t *mirror, unsigned long long *out, cudaStream_t st) {
+    if (nA == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(((int64_t)nA + 255) / 256, 2048);
+    k_footprint_sums<<<grid, 256, 0, st>>>(offA, nA, adjA, offO, mirror, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_binomial(ulonglong2 *c, int32_t *n_ovf, int32_t nmax, cudaStream_t st) {
     k_fill_i32<<<1, 32, 0, st>>>(n_ovf, kMaxPQ + 1, INT32_MAX);
     int grid = (int)std::min<int64_t>(((int64_t)nmax + 256) / 256, 4096);

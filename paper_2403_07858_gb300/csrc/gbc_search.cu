@@ -17,12 +17,13 @@ namespace gbc {
 
 thread_local int t_launches = 0;
 
-// For |L| >= 4 each root also keeps T: for each of its kTPos most shared
-// positions, the bitmap of the candidates containing it (the transpose of the
-// first two word pairs of R), placed after the root's S block.  T is stored
-// word-interleaved: word w of the kTPos rows sits together (kTPos words), so the
-// lanes of a warp that read word w of different rows share cache sectors.
-constexpr int kTPos = 128;
+// For |L| >= 4 each root also keeps T, the transpose of its R block: for each
+// position i of N(u) (P = row_stride(d) * 32 rows, the width of an R row in
+// bits), the bitmap T_i of the candidates whose R row holds i, placed after the
+// root's S block.  T is stored word-interleaved: word w of the P rows sits
+// together (P words), so the lanes of a warp that read word w of different rows
+// share cache sectors.
+__host__ __device__ __forceinline__ int64_t t_rows(int32_t d) { return (int64_t)row_stride(d) * 32; }
 
 
 // ---------------------------------------------------------------------------
@@ -347,7 +348,7 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
             const int32_t np = __ldcg(&pm[i]);
             const int64_t x = -1 - v;
             atomicOr(&Rb[2 * ((int64_t)(np >> 6) * c + x) + ((np >> 5) & 1)], 1u << (np & 31));
-            if (Tb && np < kTPos) atomicOr(&Tb[(int64_t)(x >> 5) * kTPos + np], 1u << (x & 31));
+            if (Tb) atomicOr(&Tb[(int64_t)(x >> 5) * t_rows(d) + np], 1u << (x & 31));
         }
     });
     G::sync();
@@ -475,7 +476,7 @@ __device__ __forceinline__ void root_sizes(const CountArgs &a, int64_t r, int64_
     if (cc < a.k - 1 || cc == 0) return;
     c = cc;
     wr = (int64_t)cc * row_stride(a.g.degA[r]);
-    wl = a.k >= 4 ? (int64_t)(cc + kTPos) * ((cc + 31) >> 5) : 0;
+    wl = a.k >= 4 ? (cc + t_rows(a.g.degA[r])) * ((cc + 31) >> 5) : 0;
 }
 
 template <typename T>
@@ -688,6 +689,16 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
             atomic_add_u128(a.acc, acc, a.status);
         }
     }
+    // The last warp to leave publishes the count when nothing is left for the
+    // enumeration: every |L| = 3 count, and larger ones with no live unit.
+    if (a.done && lane == 0) {
+        __threadfence();
+        const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+        if (atomicAdd(a.fin, 1) == warps - 1) {
+            __threadfence();
+            if (a.k == 3 || *(volatile int32_t *)a.n_units == 0) publish_done(a);
+        }
+    }
 }
 
 cudaError_t launch_pairs(const CountArgs &a, int n_sms, cudaStream_t st) {
@@ -734,8 +745,9 @@ constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word
 struct EnumLayout {
     int wr, wl;     // row capacities in words (both even)
     int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
-    // per warp: parents (kParents x uint4) | leaf masks | leaf tags | levels x (CR | CL | xs) | scalars
-    __host__ __device__ int staging_words() const { return kParents * 4 + 2 * kLeafList; }
+    // per warp: parents (kParents x uint4) | their word indices (kParents) | leaf masks | leaf tags |
+    // levels x (CR | CL | xs) | scalars
+    __host__ __device__ int staging_words() const { return kParents * 5 + 2 * kLeafList; }
     __host__ __device__ int level_words() const { return wr + wl + 32; }
     __host__ __device__ int warp_words() const {
         return (staging_words() + levels * level_words() + 3 * kMaxPQ + 2 + 3) & ~3;
@@ -795,7 +807,7 @@ __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c
 constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never above 2^128)
 
 template <bool STATS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, int32_t *queue, EnumLayout lay,
             uint32_t *gstack) {
     extern __shared__ __align__(16) uint32_t smem_stack[];
@@ -818,8 +830,9 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     const CountArgs &a0 = jobs[0];  // holds the batch-wide deadline and status
     uint32_t *wbase = gstack ? gstack + ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * lay.warp_words()
                              : smem_stack + (int64_t)wib * lay.warp_words();
-    uint4 *PAR = reinterpret_cast<uint4 *>(wbase);              // C_R of the staged leaf parents
-    uint32_t *LM = wbase + kParents * 4;                        // staged nonzero leaf words
+    uint4 *PAR = reinterpret_cast<uint4 *>(wbase);              // C_R of the staged leaf parents: up to
+    uint32_t *PARI = wbase + kParents * 4;                      // four nonzero words, and their word indices
+    uint32_t *LM = PARI + kParents;                             // staged nonzero leaf words
     uint32_t *LT = LM + kLeafList;                              // their tags: slot << kTagShift | word
     uint32_t *base = wbase + lay.staging_words();
     int32_t *cursor = reinterpret_cast<int32_t *>(base + lay.levels * lay.level_words());
@@ -839,7 +852,20 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         if (guidx >= total_units) break;
         const int2 unit = units[guidx];  // (job, global candidate index), largest subtrees first
         const CountArgs &a = jobs[unit.x];
-        if (__shfl_sync(kFull, (int)past_deadline(a), 0)) continue;  // this job ran out of time: drop its units
+        // the warp that finishes a count's last unit publishes the count
+        auto unit_done = [&]() {
+            if (a.done && lane == 0) {
+                __threadfence();
+                if (atomicAdd(a.fin + 1, 1) + 1 == *(volatile int32_t *)a.n_units) {
+                    __threadfence();
+                    publish_done(a);
+                }
+            }
+        };
+        if (__shfl_sync(kFull, (int)past_deadline(a), 0)) {  // this job ran out of time: drop its units
+            unit_done();
+            continue;
+        }
         const int k = a.k, kq = a.kq;
         const bool smem_binom = kq == kq0;
         unsigned long long words = 0;  // words this lane loaded for children (span-truncated; statistics only)
@@ -853,7 +879,11 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         const int32_t WL = (int32_t)((c + 31) >> 5);
         const uint2 *Rp = reinterpret_cast<const uint2 *>(a.R + a.r_off[r]);
         const uint32_t *St = a.S + a.s_off[r];
-        const uint32_t *Tb = St + (int64_t)c * WL;  // T: candidates per shared position
+        const uint32_t *Tb = St + (int64_t)c * WL;  // T: candidates per position
+        const int64_t P = t_rows(d);                // T rows of the root
+        const uint32_t *Rw = reinterpret_cast<const uint32_t *>(Rp);
+        // word wi of R row x (rows are stored word-major in pairs)
+        auto r_word = [&](int32_t x, uint32_t wi) { return Rw[2 * ((int64_t)(wi >> 1) * c + x) + (wi & 1u)]; };
         u128 unit_acc = 0;
         // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
         {
@@ -869,7 +899,9 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         // M) per lane.  The leaves' counts |C_R(y) & R_x| for all x of the word
         // are summed bit-sliced: for each position i of C_R(y) the word T_i[w]
         // of candidates containing i is added into 4-bit vertical counters, and
-        // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.
+        // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.  A parent's
+        // C_R(y) is kept as its (at most four) nonzero words with their word
+        // indices in N(u)'s position order, so it may lie anywhere in the row.
         auto count_leaves = [&](int n_staged) {
             for (int e0 = 0; e0 < n_staged; e0 += 32) {
                 const int e = e0 + lane;
@@ -877,7 +909,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     const uint32_t M = LM[e], tg = LT[e];
                     const int w = (int)(tg & ((1u << kTagShift) - 1u));
                     const uint4 cy = PAR[tg >> kTagShift];
-                    const uint32_t *Tw = Tb + (int64_t)w * kTPos;  // word w of every T row
+                    const uint32_t ix = PARI[tg >> kTagShift];      // word index of cy.x .. cy.w, 8 bits each
+                    const uint32_t *Tw = Tb + (int64_t)w * P;       // word w of every T row
                     const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
                     if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
                     if (m < 16) {
@@ -885,16 +918,17 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
 #pragma unroll
                         for (int qw = 0; qw < 4; ++qw) {
                             uint32_t bits = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
+                            const int wb = (int)((ix >> (8 * qw)) & 0xffu) << 5;  // first position of the word
                             // two positions per step: a carry-save add of both T words
                             // (sum into b0, majority carry into b1..b3); the leaf mask M
                             // is applied once, when the counts are read
                             while (bits) {
-                                const int i1 = (qw << 5) + __ffs(bits) - 1;
+                                const int i1 = wb + __ffs(bits) - 1;
                                 bits &= bits - 1;
                                 const uint32_t t1 = Tw[i1];
                                 uint32_t t2 = 0u;
                                 if (bits) {
-                                    const int i2 = (qw << 5) + __ffs(bits) - 1;
+                                    const int i2 = wb + __ffs(bits) - 1;
                                     bits &= bits - 1;
                                     t2 = Tw[i2];
                                 }
@@ -920,16 +954,20 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                             }
                         }
                     } else {
-                        // a wide C_R(y): the leaves one by one (C_R(y) has bits in
-                        // its second word pair only if R has two pairs)
-                        const bool two = (cy.z | cy.w) != 0u;
+                        // |C_R(y)| >= 16 (beyond the 4-bit counters): the leaves one by one
                         uint32_t bits = M;
                         while (bits) {
                             const int32_t x = (w << 5) + __ffs(bits) - 1;
                             bits &= bits - 1;
-                            int nx = popc2(make_uint2(cy.x, cy.y), Rp[x]);
-                            if (two) nx += popc2(make_uint2(cy.z, cy.w), Rp[c + x]);
-                            if (STATS) words += two ? 4 : 2;
+                            int nx = 0;
+#pragma unroll
+                            for (int qw = 0; qw < 4; ++qw) {
+                                const uint32_t cw = qw == 0 ? cy.x : (qw == 1 ? cy.y : (qw == 2 ? cy.z : cy.w));
+                                if (cw) {
+                                    nx += __popc(cw & r_word(x, (ix >> (8 * qw)) & 0xffu));
+                                    if (STATS) words += 1;
+                                }
+                            }
                             if (nx >= kq) {
                                 if (STATS) st_passed[1] += 1;
                                 if (smem_binom && nx < kSmemBinom) add_u128(unit_acc, s_binom[nx], ovf);
@@ -995,9 +1033,14 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 // they come from, so every lane evaluates leaves on every step.
                 // The lists carry over from batch to batch and node to node of
                 // the unit and are expanded when full or when the unit ends.
+                // C_R(y) is staged as its nonzero words with their indices, so a
+                // node whose C_R spans more than two word pairs stages like the
+                // others; a C_R(y) with more than four nonzero words (or one past
+                // word 255) has its leaves walked by its own lane instead.
                 int32_t y = 0;
-                bool py = false;
+                bool py = false, narrow = true;
                 uint4 cy = make_uint4(0, 0, 0, 0);
+                uint32_t ix = 0x03020100u;  // word indices of cy.x .. cy.w
                 if (lane < got) {
                     y = XS(lv)[lane];
                     int ny = 0;
@@ -1006,11 +1049,33 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                         if (sp > 1) { const uint2 v = and2(cr[1], Rp[c + y]); cy.z = v.x; cy.w = v.y; }
                         ny = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
                     } else {
-                        for (int pw = 0; pw < sp; ++pw) ny += popc2(cr[pw], Rp[pw * c + y]);
+                        int nw = 0;
+                        for (int pw = 0; pw < sp; ++pw) {
+                            const uint2 v = and2(cr[pw], Rp[pw * c + y]);
+                            ny += __popc(v.x) + __popc(v.y);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const uint32_t wv = h ? v.y : v.x;
+                                if (wv) {
+                                    const uint32_t wi = 2u * (uint32_t)pw + (uint32_t)h;
+                                    if (nw < 4 && wi < 256u) {
+                                        if (nw == 0) cy.x = wv;
+                                        else if (nw == 1) cy.y = wv;
+                                        else if (nw == 2) cy.z = wv;
+                                        else cy.w = wv;
+                                        ix = (ix & ~(0xffu << (8 * nw))) | (wi << (8 * nw));
+                                    } else {
+                                        narrow = false;
+                                    }
+                                    ++nw;
+                                }
+                            }
+                        }
                     }
                     py = ny >= kq;
                     if (STATS) words += 2 * sp;
                 }
+                const bool ps = py && narrow;  // staged for phase B
                 if (STATS) {
                     const unsigned pm = __ballot_sync(kFull, py);
                     if (lane == 0) {
@@ -1021,16 +1086,16 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     }
                 }
                 const int lo_y = (y + 1) >> 5;
-                const int lo_min = __reduce_min_sync(kFull, py ? lo_y : (int)WL);  // first word any passing child stages
-                if (sp <= 2) {
-                    if (lo_min < WL) {  // else no passing child has a leaf after it
-                        const unsigned pm = __ballot_sync(kFull, py);
+                const int lo_min = __reduce_min_sync(kFull, ps ? lo_y : (int)WL);  // first word any staged child stages
+                {
+                    if (lo_min < WL) {  // else no staged child has a leaf after it
+                        const unsigned pm = __ballot_sync(kFull, ps);
                         const int slot = npar + __popc(pm & ((1u << lane) - 1u));
-                        if (py) PAR[slot] = cy;
+                        if (ps) { PAR[slot] = cy; PARI[slot] = ix; }
                         npar += __popc(pm);  // <= kParents: at most kParents - 32 before the batch
                         for (int w = lo_min; w < WL; ++w) {
                             uint32_t mk = 0;
-                            if (py && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; if (STATS) words += 1; }
+                            if (ps && w >= lo_y) { mk = cl[w] & St[(int64_t)w * c + y]; if (STATS) words += 1; }
                             const unsigned nz = __ballot_sync(kFull, mk != 0u);
                             if (mk) {
                                 const int at = nl + __popc(nz & ((1u << lane) - 1u));
@@ -1048,8 +1113,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                             }
                         }
                     }
-                } else if (py) {
-                    // wide C_R (rare): the lane walks its own leaves, C_R(y) & R_x re-read per leaf
+                }
+                if (py && !narrow) {
+                    // C_R(y) spread over more than four words (rare): the lane walks its
+                    // own leaves, C_R(y) & R_x re-read per leaf
                     for (int w = lo_y; w < WL; ++w) {
                         uint32_t bits = cl[w] & St[(int64_t)w * c + y];
                         if (STATS) words += 1;
@@ -1119,6 +1186,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (a.per_root) atomic_add_u128(a.per_root + 2 * (int64_t)r, s, a.status);
             if (STATS) atomicAdd(a.enum_words, words);
         }
+        unit_done();
         ovf = false;
     }
     if (STATS) {
