@@ -154,7 +154,8 @@ typedef struct {
     int64_t enum_words;         /* words the enumeration kernel actually loaded for the
                                    children it evaluated (C_R read up to its span; stats) */
     int32_t launches;           /* CUDA kernels this count launched */
-    int32_t reserved_i;
+    int32_t pieces;             /* root ranges the count ran in: > 1 when its search scratch exceeded
+                                   the context's budget and it ran in independent pieces (Sec. VI) */
     int64_t words_enum;         /* the part of words_r + words_l that belongs to the nodes the
                                    enumeration kernel evaluates (|L| >= 3; stats) */
 } gbc_count_info;

@@ -72,7 +72,7 @@ class CountInfo(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64),
                 ("ms_candidates", ctypes.c_float), ("ms_pairs", ctypes.c_float),
                 ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
+                ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("pieces", ctypes.c_int32),
                 ("words_enum", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
@@ -94,6 +94,7 @@ class CountInfo(ctypes.Structure):
             "enum_words": int(self.enum_words),
             "words_enum": int(self.words_enum),
             "launches": int(self.launches),
+            "pieces": int(self.pieces),
         }
 
 

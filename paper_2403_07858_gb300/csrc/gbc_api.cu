@@ -573,6 +573,7 @@ struct Job {
     bool trivial = false;
     size_t scratch_bytes = 0;  // device scratch held while this job ran
     size_t base_bytes = 0;     // scratch of the root classification and scans (before the waves)
+    int pieces = 1;            // root ranges the count ran in (> 1: its scratch exceeded the budget)
     gbc_status st = GBC_OK;
     char err[256] = "";
     void set_error(gbc_status s, const char *fmt, ...) {
@@ -742,6 +743,9 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         a.binom = BinomTable{g->binom, g->n_ovf, g->binom_nmax};
         a.root_begin = 0;
         a.root_end = a.g.nA;
+        a.lib_begin = 0;
+        a.lib_end = a.g.nA;
+        a.cand_base = 0;
         if (opt && opt->root_end > opt->root_begin) {
             a.root_begin = std::max(0, opt->root_begin);
             a.root_end = std::min(a.g.nA, opt->root_end);
@@ -868,6 +872,111 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         for (int i = 0; i < n; ++i)
             if (!in_todo[i]) release(i, hs[i].acc, hs[i].status);
     }
+    // A job whose search scratch exceeds the budget on its own runs in pieces:
+    // contiguous ranges of roots (library ids), cut where the exact per-root
+    // scratch (from the scans' offsets) reaches the budget, one after the
+    // other.  Roots' search trees are independent, so the pieces need nothing
+    // from each other and add into the job's sum (the closure partitioning of
+    // Sec. VI, applied to the scratch; the graph itself stays resident).
+    auto run_in_pieces = [&](int i, size_t avail) -> gbc_status {
+        Job &J = jobs[i];
+        const CountArgs &a = J.a;
+        const int64_t nA = a.g.nA;
+        const bool k4 = a.k >= 4;
+        std::vector<int64_t> co((size_t)nA + 1), ro((size_t)nA + 1), so((size_t)nA + 1);
+        CK(cudaMemcpyAsync(co.data(), a.cand_off, (size_t)(nA + 1) * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ro.data(), a.r_off, (size_t)(nA + 1) * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(so.data(), a.s_off, (size_t)(nA + 1) * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        auto pre = [&](int64_t u) -> size_t {
+            return (size_t)co[u] * 8 + (size_t)ro[u] * 4 + (k4 ? (size_t)so[u] * 4 + (size_t)co[u] * 17 : 0);
+        };
+        const int64_t nE = std::max<int64_t>(J.g->nE, 1);
+        const size_t fixed = (size_t)nE * 8 + (k4 ? sizeof(CountArgs) + 256 : 0) + 4096;
+        if (avail <= fixed) {
+            J.set_error(GBC_ERR_OOM, "gbc_count: budget %zu B below the %zu B a count of this graph needs", avail, fixed);
+            return GBC_OK;
+        }
+        const size_t room = avail - fixed;
+        std::vector<std::pair<int64_t, int64_t>> pieces;
+        for (int64_t lb = 0; lb < nA;) {
+            int64_t lo = lb, hi = nA;  // the largest end with the range's scratch within room
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) / 2;
+                if (pre(mid) - pre(lb) <= room) lo = mid;
+                else hi = mid - 1;
+            }
+            if (lo == lb) {
+                J.set_error(GBC_ERR_OOM, "gbc_count: one root needs %zu B of search scratch, more than the %zu B left",
+                            pre(lb + 1) - pre(lb), room);
+                return GBC_OK;
+            }
+            pieces.push_back({lb, lo});
+            lb = lo;
+        }
+        J.pieces = (int)pieces.size();
+        for (const auto &pc : pieces) {
+            const int64_t pb = pc.first, pe = pc.second, nc = co[pe] - co[pb];
+            if (nc == 0) continue;
+            Scratch psc(st);
+            CountArgs b = a;
+            b.lib_begin = (int32_t)pb;
+            b.lib_end = (int32_t)pe;
+            b.cand_base = co[pb];
+            b.n_cand = nc;
+            b.done = nullptr;  // released when the last piece is done
+            int32_t *cand_p = nullptr, *root_p = nullptr;
+            uint32_t *R_p = nullptr, *S_p = nullptr;
+            CK(psc.get(&b.poscnt, nE));
+            CK(psc.get(&b.posmap, nE));
+            CK(cudaMemsetAsync(b.poscnt, 0, (size_t)nE * 4, st));
+            CK(psc.get(&cand_p, nc));
+            CK(psc.get(&root_p, nc));
+            CK(psc.get(&R_p, ro[pe] - ro[pb]));
+            CK(cudaMemsetAsync(R_p, 0, (size_t)std::max<int64_t>(ro[pe] - ro[pb], 1) * 4, st));
+            // global offsets of the piece's roots land in its own buffers
+            b.cand = cand_p - co[pb];
+            b.cand_root = root_p - co[pb];
+            b.R = R_p - ro[pb];
+            int2 *u_all = nullptr, *u_sorted = nullptr;
+            uint8_t *u_bucket = nullptr;
+            int32_t *ucnt = nullptr;
+            if (k4) {
+                CK(psc.get(&S_p, so[pe] - so[pb]));
+                CK(cudaMemsetAsync(S_p, 0, (size_t)std::max<int64_t>(so[pe] - so[pb], 1) * 4, st));
+                b.S = S_p - so[pb];
+                CK(psc.get(&u_all, nc));
+                CK(psc.get(&u_sorted, nc));
+                CK(psc.get(&u_bucket, nc));
+                CK(psc.get(&ucnt, 33));
+                CK(cudaMemsetAsync(ucnt, 0, 33 * 4, st));
+                b.units_all = u_all;
+                b.units_bucket = u_bucket;
+                b.n_units_all = ucnt;
+                b.bucket_count = ucnt + 1;
+                b.job_id = 0;
+            }
+            // the pass-B and pairwise work counters start again for every piece
+            CK(cudaMemsetAsync(&d_small[i].queues[3], 0, 5 * sizeof(int32_t), st));
+            CK(launch_candidates(b, true, hs[i].tier_count, ctx->n_sms, st));
+            CK(launch_pairs(b, ctx->n_sms, st));
+            if (k4) {
+                CountArgs *d_job = nullptr;
+                int32_t *d_queue = nullptr;
+                CK(psc.get(&d_job, 1));
+                CK(psc.get(&d_queue, 1));
+                CK(cudaMemsetAsync(d_queue, 0, 4, st));
+                CK(cudaMemcpyAsync(d_job, &b, sizeof(CountArgs), cudaMemcpyHostToDevice, st));
+                CK(launch_sort_units(u_all, u_bucket, ucnt, ucnt + 1, ucnt + 17, u_sorted, nc, st));
+                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, want_stats, opt ? opt->enum_warps : 0,
+                                    (int)row_stride(a.g.maxdegA), (std::max(hs[i].cand_max, 1) + 31) / 32, a.k,
+                                    ctx->n_sms, st));
+            }
+            CK(cudaStreamSynchronize(st));  // b is read by the launch
+            J.scratch_bytes = std::max(J.scratch_bytes, sc.bytes + psc.bytes);
+        }
+        return GBC_OK;
+    };
     size_t pos = 0;
     while (pos < todo.size()) {
         Scratch wave_sc(st);
@@ -878,10 +987,12 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             const size_t need = need_of(i);
             if (used + need > budget) {
                 if (wave.empty()) {
-                    jobs[i].set_error(GBC_ERR_OOM, "gbc_count: search scratch %zu B exceeds the budget %zu B", need,
-                                      budget);
-                    const unsigned long long zero[2] = {0, 0};
-                    release(i, zero, 0);
+                    const gbc_status e = run_in_pieces(i, budget > used ? budget - used : 0);
+                    if (e != GBC_OK) return e;
+                    if (jobs[i].st != GBC_OK) {
+                        const unsigned long long zero[2] = {0, 0};
+                        release(i, zero, 0);
+                    }
                     continue;
                 }
                 break;
@@ -1045,6 +1156,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         inf.ms_total = tm.between(0, 3);
         inf.enum_words = (int64_t)J.h.enum_words;
         inf.launches = t_launches;
+        inf.pieces = J.pieces;
         *info = inf;
     }
     if (out) {

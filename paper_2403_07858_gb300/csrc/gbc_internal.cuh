@@ -174,7 +174,15 @@ struct CountArgs {
     BinomTable binom;
     int k;          // |L| on the anchor side
     int kq;         // |R| on the other side
-    int32_t root_begin, root_end;  // roots taken: [root_begin, root_end)
+    int32_t root_begin, root_end;  // roots taken: [root_begin, root_end) (caller's ids)
+    // A count whose search scratch exceeds the budget runs in pieces, each a
+    // contiguous range of roots in the library's ids (independent search trees,
+    // the closure partitioning of Sec. VI); pass B and the pairwise rows then
+    // take only roots in [lib_begin, lib_end), whose candidates are the global
+    // candidate indices [cand_base, cand_base + n_cand).  R, S, cand and
+    // cand_root point so that the piece's global offsets land in its buffers.
+    int32_t lib_begin, lib_end;
+    int64_t cand_base;
     // root classification
     int32_t *omega;          // [nA] oriented wedge count of each root
     int32_t *tier_list;      // 3 lists of roots, each of capacity nA

@@ -376,7 +376,7 @@ k_cand_warp(CountArgs a) {
         idx = __shfl_sync(kFull, idx, 0);
         if (idx >= n || __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
         const int32_t u = a.tier_list[idx];
-        if (BUILD && a.cand_count[u] < a.k - 1) continue;
+        if (BUILD && (a.cand_count[u] < a.k - 1 || u < a.lib_begin || u >= a.lib_end)) continue;
         process_root<1, BUILD>(a, u, my_keys, my_vals, my_sort, s_int[w], acc, ovf);
     }
     if (!BUILD && a.k == 2 && lane == 0) {
@@ -419,7 +419,7 @@ k_cand_cta(CountArgs a) {
         __syncthreads();
         if (idx >= n) break;
         const int32_t u = a.tier_list[(int64_t)tier * a.g.nA + idx];
-        if (BUILD && a.cand_count[u] < a.k - 1) continue;
+        if (BUILD && (a.cand_count[u] < a.k - 1 || u < a.lib_begin || u >= a.lib_end)) continue;
         process_root<kCtaThreads / 32, BUILD>(a, u, keys, vals, sortbuf, s_int, acc, ovf);
     }
     if (!BUILD && a.k == 2 && (threadIdx.x & 31) == 0) {
@@ -617,6 +617,7 @@ __global__ void __launch_bounds__(256) k_pairs(CountArgs a) {
         if (lane == 0) gidx = atomicAdd(a.queues + 6, 1);
         gidx = __shfl_sync(kFull, gidx, 0);
         if (gidx >= a.n_cand || __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
+        gidx += a.cand_base;  // the piece's first candidate (0 when the count runs whole)
         const int32_t r = a.cand_root[gidx];
         const int32_t j = (int32_t)(gidx - a.cand_off[r]);
         const int64_t c = a.cand_count[r];
