@@ -211,6 +211,36 @@ gbc_status gbc_count_p2_noalloc(int32_t nU, int32_t nV, const int32_t *offU_d, c
                                 gbc_u128 *out);
 
 /*
+ * Listing mode: the bicliques themselves (Alg. 1 outputs them; Sec. IV).
+ *
+ * Records, int32 words in the caller's device buffer, one per leaf of a search
+ * tree: the anchor-side set L (|L| = p with anchor U, q with anchor V; the
+ * caller's ids, the tree's root first), then m = |C_R|, then the m vertices of
+ * C_R (the common neighbourhood of L on the other side, caller's ids), with
+ * m >= q (anchor U) or m >= p (anchor V).  Every biclique (L, R) of the count
+ * is (L, a subset of C_R) of exactly one record, so the number of bicliques is
+ * the sum over records of C(m, q) (anchor U).
+ *
+ * gbc_list_begin prepares a listing of (g, p, q) from `anchor` (GBC_ANCHOR_AUTO
+ * = U): it runs the search once to size every root's records and returns the
+ * totals and the words of the largest root's records, the least buffer that
+ * drains the listing (host outputs, may be NULL).  Each gbc_list_next call writes the
+ * records of the next roots that fit entirely in buf_d (device, capacity_words
+ * int32 words, caller-owned): *words and *records (host) say how much it wrote,
+ * *done (host) becomes 1 when every record has been written.  The caller
+ * consumes the buffer between calls (back-pressure: the listing waits for the
+ * caller, nothing is dropped).  A root whose records alone exceed the buffer
+ * gives GBC_ERR_OOM (the message states the words it needs).  gbc_list_end
+ * releases the listing.  Errors: GBC_ERR_ARG, GBC_ERR_OOM, GBC_ERR_CUDA.
+ */
+typedef struct gbc_lister_s *gbc_lister_t;
+gbc_status gbc_list_begin(gbc_graph_t g, int p, int q, int anchor, gbc_lister_t *out,
+                          int64_t *total_words, int64_t *total_records, int64_t *max_root_words);
+gbc_status gbc_list_next(gbc_lister_t l, int32_t *buf_d, int64_t capacity_words, int64_t *words,
+                         int64_t *records, int *done);
+void gbc_list_end(gbc_lister_t l);
+
+/*
  * gbc_count_batch -- many counts, possibly on different graphs of this context,
  * in one pipeline: every stage runs for all jobs before the host waits, and the
  * enumeration (Alg. 1's search below the roots' children, Sec. IV) of all jobs

@@ -139,6 +139,11 @@ SIGNATURES = {
     "gbc_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServeStats)]),
     "gbc_footprint": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_int)]),
+    "gbc_list_begin": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp),
+                                      ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "gbc_list_next": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "gbc_list_end": (None, [_vp]),
     "gbc_submit": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gbc_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U128)]),
     "gbc_measure_int_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -251,6 +256,38 @@ class Graph:
         b, e = ctypes.c_size_t(), ctypes.c_int()
         _check(load_library().gbc_footprint(self._h, p, q, ctypes.byref(b), ctypes.byref(e)), "gbc_footprint")
         return int(b.value), bool(e.value)
+
+    def list_records(self, p: int, q: int, buffer=None, anchor: str = "U", min_words: int = 4096,
+                     calls: list | None = None):
+        """Yield the listed bicliques as (L, C_R) tuples of caller ids, filling the
+        int32 CUDA tensor ``buffer`` one gbc_list_next call at a time (None: one
+        of max(min_words, the largest root's records) words).  ``calls``, if
+        given, receives the (words, records) of every call."""
+        lib = load_library()
+        h = ctypes.c_void_p()
+        tw, tr, mx = _i64(), _i64(), _i64()
+        _check(lib.gbc_list_begin(self._h, p, q, ANCHORS[anchor], ctypes.byref(h), ctypes.byref(tw),
+                                  ctypes.byref(tr), ctypes.byref(mx)), "gbc_list_begin")
+        k = p if anchor == "U" else q
+        try:
+            if buffer is None:
+                import torch
+                buffer = torch.zeros(max(min_words, mx.value, 1), dtype=torch.int32, device="cuda")
+            done = ctypes.c_int(0)
+            while not done.value:
+                w, r = _i64(), _i64()
+                _check(lib.gbc_list_next(h, ctypes.c_void_p(buffer.data_ptr()), buffer.numel(), ctypes.byref(w),
+                                         ctypes.byref(r), ctypes.byref(done)), "gbc_list_next")
+                if calls is not None:
+                    calls.append((w.value, r.value))
+                words = buffer[:w.value].cpu().tolist()
+                at = 0
+                for _ in range(r.value):
+                    m = words[at + k]
+                    yield tuple(words[at:at + k]), tuple(words[at + k + 1:at + k + 1 + m])
+                    at += k + 1 + m
+        finally:
+            lib.gbc_list_end(h)
 
     def tuned_anchor(self, p: int, q: int) -> str | None:
         return _ANCHOR_NAMES.get(load_library().gbc_tuned_anchor(self._h, p, q))

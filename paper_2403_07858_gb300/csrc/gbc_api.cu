@@ -574,6 +574,13 @@ struct Job {
     size_t scratch_bytes = 0;  // device scratch held while this job ran
     size_t base_bytes = 0;     // scratch of the root classification and scans (before the waves)
     int pieces = 1;            // root ranges the count ran in (> 1: its scratch exceeded the budget)
+    // listing mode (gbc_list_*): 1 sizes every root's records, 2 writes those
+    // of roots [list_begin, list_end) (library ids) into list_out
+    int list_mode = 0;
+    int32_t list_begin = 0, list_end = 0;
+    std::vector<int64_t> *list_sizes = nullptr;        // mode 1: 2 * |anchor side| (words, records)
+    const std::vector<int64_t> *list_offsets = nullptr; // mode 2: per root of the range
+    int32_t *list_out = nullptr;                        // mode 2: device buffer
     gbc_status st = GBC_OK;
     char err[256] = "";
     void set_error(gbc_status s, const char *fmt, ...) {
@@ -815,7 +822,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
             CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
         }
-        if (a.k >= 3) {
+        if (a.k >= 3 || J.list_mode) {
             const int64_t nA = a.g.nA;
             int64_t *cand_off, *r_off, *s_off;
             CK(sc.get(&cand_off, nA + 1));
@@ -835,7 +842,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         if (!active(J)) continue;
         CountArgs &a = J.a;
         CK(launch_candidates(a, false, hs[i].tier_count, ctx->n_sms, sj(i)));
-        if (a.k >= 3)
+        if (a.k >= 3 || J.list_mode)
             CK(launch_root_offsets(a, const_cast<int64_t *>(a.cand_off), const_cast<int64_t *>(a.r_off),
                                    const_cast<int64_t *>(a.s_off), scan_tmp[i], d_small[i].totals, sj(i)));
     }
@@ -850,7 +857,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     std::vector<int> todo;
     for (int i = 0; i < n; ++i) {
         Job &J = jobs[i];
-        if (!active(J) || J.a.k < 3) continue;
+        if (!active(J) || J.a.k < 3 || J.list_mode) continue;
         J.a.n_cand = hs[i].totals[0];
         if (J.a.n_cand == 0) continue;
         if (J.a.n_cand >= INT32_MAX) {
@@ -977,6 +984,89 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         }
         return GBC_OK;
     };
+    // Listing: pass B rows for the range's roots, then the listing kernel.
+    auto run_listing = [&](int i) -> gbc_status {
+        Job &J = jobs[i];
+        CountArgs b = J.a;
+        const int64_t nA = b.g.nA;
+        const int32_t lb = J.list_begin, le = J.list_end;
+        Scratch lsc(st);
+        ListArgs L;
+        memset(&L, 0, sizeof L);
+        L.mode = J.list_mode;
+        L.begin = lb;
+        L.end = le;
+        L.callerO = J.anchor == GBC_ANCHOR_U ? J.g->callerV : J.g->callerU;
+        CK(lsc.get(&L.queue, 1));
+        CK(cudaMemsetAsync(L.queue, 0, 4, st));
+        if (L.mode == 1) {
+            CK(lsc.get(&L.sizes, 2 * std::max<int64_t>(nA, 1)));
+            CK(cudaMemsetAsync(L.sizes, 0, 16 * (size_t)std::max<int64_t>(nA, 1), st));
+        } else {
+            int64_t *offs = nullptr;
+            CK(lsc.get(&offs, std::max<int32_t>(le - lb, 1)));
+            if (le > lb)
+                CK(cudaMemcpyAsync(offs, J.list_offsets->data(), 8 * (size_t)(le - lb), cudaMemcpyHostToDevice, st));
+            L.offsets = offs;
+            L.out = J.list_out;
+        }
+        const int64_t range = le - lb;
+        int warps = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->n_sms * 32, range));
+        bool launch = range > 0;
+        if (b.k >= 2 && launch) {
+            if (!active(J)) launch = false;  // nothing to list (p > |anchor| or q > max degree)
+        }
+        if (b.k >= 2 && launch) {
+            int64_t ends[4];
+            CK(cudaMemcpyAsync(&ends[0], b.cand_off + lb, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&ends[1], b.cand_off + le, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&ends[2], b.r_off + lb, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&ends[3], b.r_off + le, 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            const int64_t nc = ends[1] - ends[0];
+            const int64_t nE = std::max<int64_t>(J.g->nE, 1);
+            int32_t *cand_p = nullptr, *root_p = nullptr;
+            uint32_t *R_p = nullptr;
+            CK(lsc.get(&b.poscnt, nE));
+            CK(lsc.get(&b.posmap, nE));
+            CK(cudaMemsetAsync(b.poscnt, 0, (size_t)nE * 4, st));
+            CK(lsc.get(&cand_p, nc));
+            CK(lsc.get(&root_p, nc));
+            CK(lsc.get(&R_p, ends[3] - ends[2]));
+            CK(cudaMemsetAsync(R_p, 0, (size_t)std::max<int64_t>(ends[3] - ends[2], 1) * 4, st));
+            b.lib_begin = lb;
+            b.lib_end = le;
+            b.cand_base = ends[0];
+            b.n_cand = nc;
+            b.cand = cand_p - ends[0];
+            b.cand_root = root_p - ends[0];
+            b.R = R_p - ends[2];
+            b.S = nullptr;
+            b.done = nullptr;
+            CK(cudaMemsetAsync(&d_small[i].queues[3], 0, 5 * sizeof(int32_t), st));
+            if (nc > 0) CK(launch_candidates(b, true, hs[i].tier_count, ctx->n_sms, st));
+            else launch = false;
+            if (launch) {
+                L.stack_words = list_stack_words(b.k, b.g.maxdegA, hs[i].cand_max);
+                warps = (int)std::max<int64_t>(1, std::min<int64_t>(warps, (int64_t(1) << 28) / L.stack_words));
+                CK(lsc.get(&L.stack, (size_t)warps * L.stack_words));
+            }
+        }
+        if (launch) CK(launch_list(b, L, warps, st));
+        if (L.mode == 1) {
+            J.list_sizes->assign(2 * (size_t)nA, 0);
+            if (nA > 0)
+                CK(cudaMemcpyAsync(J.list_sizes->data(), L.sizes, 16 * (size_t)nA, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        J.scratch_bytes = std::max(J.scratch_bytes, sc.bytes + lsc.bytes);
+        return GBC_OK;
+    };
+    for (int i = 0; i < n; ++i)
+        if (jobs[i].list_mode && jobs[i].st == GBC_OK) {
+            const gbc_status e = run_listing(i);
+            if (e != GBC_OK) return e;
+        }
     size_t pos = 0;
     while (pos < todo.size()) {
         Scratch wave_sc(st);
@@ -1241,6 +1331,115 @@ extern "C" gbc_status gbc_count_per_root(gbc_graph_t g, int p, int q, int anchor
     cudaStreamSynchronize(st);
     return s;
 }
+
+// ---------------------------------------------------------------------------
+// Listing mode (Alg. 1 outputs the bicliques themselves).  gbc_list_begin sizes
+// every root's records with one pass of the listing kernel; each
+// gbc_list_next writes the records of the next roots whose records fit in the
+// caller's buffer, so the caller drains the listing at its own pace.
+struct gbc_lister_s {
+    gbc_graph_s *g = nullptr;
+    int p = 0, q = 0, anchor = 0;
+    int64_t nA = 0;
+    std::vector<int64_t> sizes;  // (words, records) per root, library ids
+    int64_t next = 0;            // first root not yet written
+};
+
+static gbc_status run_list_job(gbc_lister_s *l, int mode, int32_t begin, int32_t end,
+                               const std::vector<int64_t> *offsets, int32_t *out) {
+    gbc_graph_s *g = l->g;
+    gbc_ctx_s *ctx = g->ctx;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<Job> jobs(1);
+    Job &J = jobs[0];
+    J.g = g;
+    J.p = l->p;
+    J.q = l->q;
+    J.anchor = l->anchor;
+    J.list_mode = mode;
+    J.list_begin = begin;
+    J.list_end = end;
+    J.list_sizes = &l->sizes;
+    J.list_offsets = offsets;
+    J.list_out = out;
+    Timer tm;
+    tm.init(false);
+    const gbc_status s = run_jobs(ctx, ctx->lane, ctx->budget, jobs, nullptr, false, tm, nullptr);
+    if (s != GBC_OK) return s;
+    if (J.st != GBC_OK) return fail(J.st, "%s", J.err);
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_list_begin(gbc_graph_t g, int p, int q, int anchor, gbc_lister_t *out,
+                                     int64_t *total_words, int64_t *total_records, int64_t *max_root_words) {
+    if (!g || !out) return fail(GBC_ERR_ARG, "gbc_list_begin: null argument");
+    if (p < 1 || q < 1 || p > GBC_MAX_PQ || q > GBC_MAX_PQ)
+        return fail(GBC_ERR_ARG, "gbc_list_begin: p=%d q=%d outside [1, %d]", p, q, GBC_MAX_PQ);
+    if (anchor == GBC_ANCHOR_AUTO) anchor = GBC_ANCHOR_U;
+    if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_list_begin: bad anchor %d", anchor);
+    gbc_lister_s *l = new gbc_lister_s();
+    l->g = g;
+    l->p = p;
+    l->q = q;
+    l->anchor = anchor;
+    l->nA = anchor == GBC_ANCHOR_U ? g->nU : g->nV;
+    const gbc_status s = run_list_job(l, 1, 0, (int32_t)l->nA, nullptr, nullptr);
+    if (s != GBC_OK) {
+        delete l;
+        return s;
+    }
+    int64_t w = 0, r = 0, mx = 0;
+    for (int64_t u = 0; u < l->nA; ++u) {
+        w += l->sizes[2 * u];
+        r += l->sizes[2 * u + 1];
+        mx = std::max(mx, l->sizes[2 * u]);
+    }
+    if (total_words) *total_words = w;
+    if (total_records) *total_records = r;
+    if (max_root_words) *max_root_words = mx;
+    *out = l;
+    return GBC_OK;
+}
+
+extern "C" gbc_status gbc_list_next(gbc_lister_t l, int32_t *buf_d, int64_t capacity_words, int64_t *words,
+                                    int64_t *records, int *done) {
+    if (!l || !words || !records || !done || capacity_words < 0 || (capacity_words > 0 && !buf_d))
+        return fail(GBC_ERR_ARG, "gbc_list_next: bad argument");
+    *words = 0;
+    *records = 0;
+    while (l->next < l->nA && l->sizes[2 * l->next] == 0) ++l->next;  // roots with nothing to list
+    if (l->next >= l->nA) {
+        *done = 1;
+        return GBC_OK;
+    }
+    const int64_t begin = l->next;
+    int64_t end = begin, w = 0, r = 0;
+    while (end < l->nA && w + l->sizes[2 * end] <= capacity_words) {
+        w += l->sizes[2 * end];
+        r += l->sizes[2 * end + 1];
+        ++end;
+    }
+    if (end == begin)
+        return fail(GBC_ERR_OOM, "gbc_list_next: the next root's records need %lld words, more than the buffer's %lld",
+                    (long long)l->sizes[2 * begin], (long long)capacity_words);
+    std::vector<int64_t> offs((size_t)(end - begin));
+    int64_t at = 0;
+    for (int64_t u = begin; u < end; ++u) {
+        offs[(size_t)(u - begin)] = at;
+        at += l->sizes[2 * u];
+    }
+    const gbc_status s = run_list_job(l, 2, (int32_t)begin, (int32_t)end, &offs, buf_d);
+    if (s != GBC_OK) return s;
+    l->next = end;
+    while (l->next < l->nA && l->sizes[2 * l->next] == 0) ++l->next;
+    *words = w;
+    *records = r;
+    *done = l->next >= l->nA ? 1 : 0;
+    return GBC_OK;
+}
+
+extern "C" void gbc_list_end(gbc_lister_t l) { delete l; }
 
 // The autotuner: for each job it times the count from both anchors (the second
 // bounded by the first's time) and keeps the faster one for later counts of the

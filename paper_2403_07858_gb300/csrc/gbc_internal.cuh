@@ -267,6 +267,23 @@ constexpr int kCtaThreads = 256;
 constexpr int kWarpTierWarps = 8;
 constexpr int kWarpTierBytes = 2 * kWarpTierSlots * 4 + kWarpTierOmega * 8;
 
+// Listing mode (gbc_list.cu): mode 1 writes each root's record words and
+// records to sizes[2u], sizes[2u+1]; mode 2 writes the records of roots
+// [begin, end) at out + offsets[u - begin].
+struct ListArgs {
+    int32_t mode;
+    int32_t begin, end;           // roots, library ids
+    int32_t *queue;               // zeroed work counter
+    int64_t *sizes;               // mode 1: [2 * nA]
+    const int64_t *offsets;       // mode 2: [end - begin]
+    int32_t *out;                 // mode 2: the caller's buffer
+    const int32_t *callerO;       // the caller's id of every other-side vertex
+    uint32_t *stack;              // per-warp depth-first stacks
+    int64_t stack_words;          // words of one warp's stack
+};
+int64_t list_stack_words(int k, int32_t maxdeg, int64_t cand_max);
+cudaError_t launch_list(const CountArgs &a, const ListArgs &L, int warps, cudaStream_t st);
+
 // Launchers (gbc_kernels.cu).  All run on `st`; none synchronises.
 cudaError_t launch_validate_offsets(const int32_t *off, int32_t n, int64_t nE, uint32_t *status, cudaStream_t st);
 cudaError_t launch_validate_rows(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other,

@@ -340,7 +340,7 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
     // contiguous c * 8 B block (deep C_R spans rarely go past it).
     uint32_t *Rb = a.R + a.r_off[u];
     const int32_t WLc = (c + 31) >> 5;
-    uint32_t *Tb = a.k >= 4 ? a.S + a.s_off[u] + (int64_t)c * WLc : nullptr;
+    uint32_t *Tb = a.k >= 4 && a.S ? a.S + a.s_off[u] + (int64_t)c * WLc : nullptr;  // no S in listing mode
     for_each_wedge<NW>(g, u, [&](int32_t w, int32_t i) {
         const int32_t slot = table_find(keys, log2slots, w, a.status);
         const int32_t v = slot >= 0 ? vvals[slot] : 0;
