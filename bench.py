@@ -47,9 +47,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbc", choices=["gbc", "reference"])
     ap.add_argument("--pq", default="2,3,4,5,6", help="p = q values of one step")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the dense-core timings and the batched-vs-plain comparison of the default line")
     ap.add_argument("--no-roofline", action="store_true",
                     help="skip the untimed statistics pass and microbenchmarks behind the roofline")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
@@ -69,19 +70,32 @@ def _peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle on a bounded sample (cpu_baseline leg and the reference arm).
-def _oracle_worker(q_out, ready_q, start_evt, graph_args, anchor, k, roots):
+# CPU oracle (cpu_baseline leg and the reference arm).  The oracle counted every
+# workload count to completion once, on all roots, with each root's time
+# (tests/golden/full_counts.json, written by tests/golden/oracle_full_counts.py).
+# Here it re-times a fixed sample of those roots -- the same roots every run,
+# drawn with probability proportional to their time -- on this host's cores, and
+# scales the full run by the ratio of the two timings of the same roots:
+#     est. core-seconds here = (sum of sample times here / sum of their stored
+#     times) x stored core-seconds of the full count,
+# and wall time on `cores` processes = that / cores.
+FULL_COUNTS = os.path.join(ROOT, "tests", "golden", "full_counts.json")
+
+
+def _oracle_pool_init(graph_fn):
+    global _ORC_G
     sys.path.insert(0, ROOT)
     import oracle
-    g = bipgen.chung_lu(*graph_args)
     oracle.build()
-    ready_q.put(1)
-    start_evt.wait()
-    for r in roots:
-        t0 = time.perf_counter()
-        oracle.count(g, k, k, anchor=anchor, roots=(r, r + 1))
-        q_out.put((r, time.perf_counter() - t0))
-    q_out.put(None)
+    _ORC_G = getattr(bipgen, graph_fn)()
+
+
+def _oracle_root_task(args):
+    import oracle
+    k, q, anchor, root = args
+    t0 = time.perf_counter()
+    oracle.count(_ORC_G, k, q, anchor=anchor, roots=(root, root + 1))
+    return args, time.perf_counter() - t0
 
 
 def host_cores():
@@ -91,54 +105,60 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(pqs, anchors, budget_s, seed, workers=1):
-    """Time the oracle on seeded uniform samples of roots, one (p,q) after the
-    other, each for budget_s / len(pqs) seconds, on `workers` processes that
-    share one permutation of the roots; extrapolate to all roots from the roots
-    finished per second of wall time."""
-    graph_args = (2, 200_000, 100_000, 2_000_000, 2.0, 2.3)
-    n_roots = {"U": 200_000, "V": 100_000}
-    ctx = mp.get_context("spawn")
-    per = budget_s / len(pqs)
-    est_s, detail = 0.0, []
-    for k, anchor in zip(pqs, anchors):
-        rng = __import__("numpy").random.default_rng(seed + k)
-        roots = rng.permutation(n_roots[anchor])[:100_000].tolist()
-        q, ready_q, start_evt = ctx.Queue(), ctx.Queue(), ctx.Event()
-        procs = [ctx.Process(target=_oracle_worker,
-                             args=(q, ready_q, start_evt, graph_args, anchor, k, roots[w::workers]), daemon=True)
-                 for w in range(workers)]
-        for pr in procs:
-            pr.start()
-        # every worker regenerates the graph first; the clock starts when all are ready
-        for _ in range(workers):
-            ready_q.get(timeout=300)
-        t0 = time.perf_counter()
-        start_evt.set()
-        deadline = t0 + per
-        done, spent, finished = 0, 0.0, 0
-        while finished < workers:
-            try:
-                item = q.get(timeout=max(0.0, deadline - time.perf_counter()))
-            except Exception:
-                break
-            if item is None:
-                finished += 1
+class OracleSample:
+    """The stored fixed samples of a workload's counts, timed on this host's
+    cores by one spawned oracle process per core (the graph is drawn once per
+    process, before the clock starts)."""
+
+    def __init__(self, workload: str, graph_fn: str, pairs, cores: int):
+        rec = json.load(open(FULL_COUNTS))[workload]["counts"]
+        self.pairs, self.missing, self.stored = [], [], {}
+        for p, q in pairs:
+            r = rec.get(f"{p},{q}")
+            if r is None or "count" not in r:
+                self.missing.append((p, q))
                 continue
-            done += 1
-            spent += item[1]
-            if time.perf_counter() >= deadline:
-                break
+            self.pairs.append((p, q))
+            self.stored[(p, q)] = r
+        # p, q as the oracle takes them from the stored anchor
+        self.tasks = []
+        for p, q in self.pairs:
+            r = self.stored[(p, q)]
+            for root in r["pps_sample"]["roots"]:
+                self.tasks.append((p, q, r["anchor"], int(root)))
+        x86 = {(p, q, r["anchor"], int(root)): float(t)
+               for (p, q), r in self.stored.items()
+               for root, t in zip(r["pps_sample"]["roots"], r["pps_sample"]["oracle_s"])}
+        self.stored_s = x86
+        self.tasks.sort(key=lambda t: -x86[t])  # longest first
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_pool_init, initargs=(graph_fn,))
+        self.pool.map(_oracle_root_task, [self.tasks[-1]] * cores if self.tasks else [])  # workers ready
+
+    def run(self):
+        """One timed pass over every sample root: (wall seconds, per-pair estimate of
+        the whole count's wall time on `cores` processes, detail)."""
+        t0 = time.perf_counter()
+        done = self.pool.map(_oracle_root_task, self.tasks, chunksize=1)
         wall = time.perf_counter() - t0
-        in_flight = sum(1 for pr in procs if pr.is_alive())
-        for pr in procs:
-            pr.kill()
-        for pr in procs:
-            pr.join()
-        est = wall * n_roots[anchor] / max(1, done + in_flight)
-        est_s += est
-        detail.append(f"p=q={k} anchor {anchor}: {done} roots in {wall:.1f} s on {workers} processes")
-    return est_s, detail
+        here = {}
+        for args, t in done:
+            here.setdefault((args[0], args[1]), []).append((t, self.stored_s[args]))
+        est, detail = {}, []
+        for p, q in self.pairs:
+            r = self.stored[(p, q)]
+            h = here.get((p, q), [])
+            ratio = sum(t for t, _ in h) / max(1e-12, sum(x for _, x in h))
+            core_s = ratio * float(r["oracle_core_s"])
+            est[(p, q)] = max(core_s / self.cores, ratio * float(r["max_root_s"]))
+            detail.append(f"({p},{q}): {len(h)} roots, here/stored time {ratio:.3f}, "
+                          f"est. {core_s:.0f} core-s here; stored full run {r['oracle_wall_s']:.0f} s wall on "
+                          f"{r['cores']} cores ({r['oracle_core_s']:.0f} core-s)")
+        return wall, est, detail
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 # ---------------------------------------------------------------------------
@@ -210,6 +230,15 @@ def main():
         serve_workload(args, rank, world, local)
         return
 
+    # host-side inputs first: process pools are spawned before CUDA starts
+    g = bipgen.workload_powerlaw_2m()
+    extras = not args.no_extras and world == 1
+    dense = bipgen.workload_dense_core() if extras else None
+    batch_jobs = _batch_jobs() if extras else None
+    orc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        orc = OracleSample("powerlaw2m", "workload_powerlaw_2m", [(k, k) for k in pqs], host_cores())
+
     import torch
     import paper_2403_07858_gb300 as gbc
     dist = None
@@ -219,8 +248,6 @@ def main():
     torch.cuda.set_device(local)
     gbc.build()
 
-    g = bipgen.workload_powerlaw_2m()
-    sha = bipgen.graph_sha256(g)
     ctx = gbc.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
@@ -236,6 +263,7 @@ def main():
     for k in pqs:
         n, info = h.count_ex(k, k)
         ref_counts[k], anchors[k] = n, info["anchor"]
+        assert anchors[k] == _auto_anchor(g, k)  # the config states the library's choice
     for _ in range(args.warmup):
         for k in pqs:
             assert h.count(k, k) == ref_counts[k]
@@ -345,32 +373,114 @@ def main():
                                                    / micro["and_popc_words_per_s"],
                     "l2_and_popc_stream_gbs": micro["l2_bytes_per_s"] / 1e9}}
 
+    # ---- the dense-core and the 256-graph batch workloads (extra keys of the line)
+    dense_line = dense_core_timing(ctx, dense, flush) if extras else None
+    batch_line = batch_comparison(ctx, batch_jobs, flush) if extras else None
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cores = host_cores()
-        est_s, detail = oracle_sample(pqs, [anchors[k] for k in pqs], args.cpu_budget, seed=7, workers=cores)
-        cpu = {"value": est_s * 1e3 / len(pqs), "unit": "ms", "cores": cores, "kind": "oracle",
-               "sample": "seeded uniform sample of roots per (p,q) shared by one oracle process per host core, "
-                         "wall time scaled by (all roots / roots finished); " + "; ".join(detail)}
+    if orc is not None:
+        wall, est, detail = orc.run()
+        orc.close()
+        per_count = [est[(k, k)] for k in pqs if (k, k) in est]
+        cpu = {"value": 1e3 * statistics.mean(per_count) if per_count else None, "unit": "ms",
+               "cores": orc.cores, "kind": "oracle",
+               "sample": f"fixed sample of {len(orc.tasks)} roots (the same every run, drawn with probability "
+                         f"proportional to their time in the stored full oracle run), timed here in {wall:.1f} s "
+                         f"on {orc.cores} processes; each whole count = stored full-run core-seconds x "
+                         f"(time here / stored time of the same roots) / cores; " + "; ".join(detail)
+                         + ("; no stored full run for " + str(orc.missing) if orc.missing else "")}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 bitmaps, u128 counts", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph_sha256": sha, "counts_per_step": len(pqs),
-                       "anchor": {str(k): anchors[k] for k in pqs},
-                       "l2": "512 MiB written between timed steps (outside the events); per-count "
-                             "scratch also exceeds L2",
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "config": sweep_config(g, pqs, world),
             "counts": {str(k): str(ref_counts[k]) for k in pqs},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": launches,
+            "dense_core": dense_line, "batch": batch_line,
         }
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _batch_job(seed):
+    return bipgen.batch_job(seed)
+
+
+def _batch_jobs():
+    """The 256 jobs of the batch workload, drawn in a spawned process pool."""
+    with mp.get_context("spawn").Pool(min(32, host_cores())) as pool:
+        return pool.map(_batch_job, range(100, 356), chunksize=1)
+
+
+DENSE_PAIRS = [(4, 4), (6, 6), (8, 8), (4, 8)]
+
+
+def dense_core_timing(ctx, g, flush, reps=2):
+    """Device time of each count of the dense-core workload (50k x 50k ER, 5M
+    edges, 20 planted K_{40,40}), graph resident, one untimed count first; each
+    count checked against the oracle's stored whole count."""
+    import torch
+    stored = json.load(open(FULL_COUNTS))["dense_core"]
+    assert stored["sha256"] == bipgen.graph_sha256(g)
+    h = ctx.load(g)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "Erdos-Renyi seed 3, 50000 x 50000, 5000000 edges + 20 planted K_{40,40} "
+                       f"({g.n_edges} edges)", "reps": reps, "pairs": {}}
+    for p, q in DENSE_PAIRS:
+        n = h.count(p, q)
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            assert h.count(p, q) == n
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out["pairs"][f"{p},{q}"] = {"ms": statistics.mean(ms), "count": str(n),
+                                    "equals_oracle": n == int(stored["counts"][f"{p},{q}"]["count"])}
+    h.close()
+    return out
+
+
+def batch_comparison(ctx, jobs, flush, reps=3):
+    """Queries/s of one gbc_count_batch over the 256-graph batch against 256 plain
+    gbc_count calls on the same resident graphs (autotuned anchors, identical
+    counts asserted), `reps` timed passes each after one untimed pass."""
+    import torch
+    hs = [ctx.load(g) for g, _, _ in jobs]
+    ps = [p for _, p, _ in jobs]
+    qs = [q for _, _, q in jobs]
+    ctx.autotune(hs, ps, qs, time_limit_ms=30_000)
+    ref = [h.count(p, q) for h, p, q in zip(hs, ps, qs)]
+    assert ctx.count_batch(hs, ps, qs) == ref
+
+    def timed(fn):
+        out = []
+        for _ in range(reps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+            assert res == ref
+        return statistics.mean(out)
+
+    t_batch = timed(lambda: ctx.count_batch(hs, ps, qs))
+    t_plain = timed(lambda: [h.count(p, q) for h, p, q in zip(hs, ps, qs)])
+    for h in hs:
+        h.close()
+    return {"workload": BATCH_WORKLOAD, "queries": len(jobs), "reps": reps,
+            "batched_qps": len(jobs) / t_batch, "plain_qps": len(jobs) / t_plain,
+            "batched_over_plain": t_plain / t_batch, "identical_counts": True,
+            "how": "host wall clock around each pass (synchronised), graphs resident"}
 
 
 BATCH_WORKLOAD = ("256 chung-lu graphs, seeds 100..355: |E| = 10^U[3,6], |U|:|V| ratio U[0.25,4], "
@@ -497,7 +607,7 @@ def serve_workload(args, rank, world, local):
             alone[(gi, p, q)] = "timeout"
         serv_ms.append((time.perf_counter() - t) * 1e3)
     mu = 1e3 / statistics.mean(serv_ms)  # queries/s of one stream
-    ctx.serve_start(workers=2, max_batch=64, max_queue=100_000, time_limit_ms=lim)
+    ctx.serve_start(workers=4, max_batch=64, max_queue=100_000, time_limit_ms=lim)
     rng = np.random.default_rng(601)
     rates, mismatches = [], 0
     for ri, f in enumerate([0.25, 0.5, 1.0, 2.0, 4.0]):
@@ -529,16 +639,22 @@ def serve_workload(args, rank, world, local):
             fu.result()
         pool.shutdown()
         lat = [done_at[i] - arrivals[i] for i in range(len(qs))]
+        answered = [i for i in range(len(qs)) if isinstance(status[i], int)]
+        lat_ok = [lat[i] for i in answered] or [float("nan")]
         for i, key in enumerate(qs[:24]):
             # a query that finished alone may pass its deadline in a crowded mix:
             # only two finished counts can disagree
             if isinstance(alone[key], int) and isinstance(status[i], int) and status[i] != alone[key]:
                 mismatches += 1
         span = max(done_at) - arrivals[0]
-        rates.append({"offered_qps": lam, "factor": f, "queries": len(qs),
-                      "served_qps": len(qs) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                      "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                      "timeouts": sum(1 for x in status if x == "timeout")})
+        rates.append({"offered_qps": lam, "factor": f, "queries": len(qs), "answered": len(answered),
+                      "served_qps": len(answered) / span,
+                      "p50_ms": 1e3 * float(np.percentile(lat_ok, 50)),
+                      "p99_ms": 1e3 * float(np.percentile(lat_ok, 99)),
+                      "p99_all_ms": 1e3 * float(np.percentile(lat, 99)),
+                      "timeouts": sum(1 for x in status if x == "timeout"),
+                      "errors": sum(1 for x in status if isinstance(x, str) and x != "timeout")})
+    stats = ctx.serve_stats()
     ctx.serve_stop()
     best = max(r["served_qps"] for r in rates)
     if rank == 0:
@@ -549,9 +665,12 @@ def serve_workload(args, rank, world, local):
                                       f"{graphs[0].n_u}/{graphs[0].n_v}/{graphs[0].n_edges} vertices/edges, "
                                       f"seeds 501..507 |E| log-uniform in [1e5,1e7] x {args.serve_scale}; "
                                       "queries: graph uniform, p,q uniform in {2..8}, Poisson arrivals",
-                          "scale": args.serve_scale, "per_request_limit_ms": lim, "workers": 2,
+                          "scale": args.serve_scale, "per_request_limit_ms": lim, "workers": 4,
                           "graph_generation_s": t_gen},
-               "single_stream_qps": mu, "rates": rates, "served_equals_alone_mismatches": mismatches}
+               "single_stream_qps": mu, "rates": rates, "served_equals_alone_mismatches": mismatches,
+               "value_is": "answered queries/s (requests past their deadline are counted apart, as timeouts), "
+                           "best over the rates; p50/p99 over answered requests, p99_all over all",
+               "server": stats}
         print(json.dumps(out), flush=True)
     for h in hs:
         h.close()
@@ -598,28 +717,44 @@ def _auto_anchor(g, k):
     return "U" if wedges_u <= wedges_v else "V"
 
 
+def sweep_config(g, pqs, world=1):
+    """The config object of the sweep line (both arms print the same)."""
+    return {"workload": WORKLOAD, "graph_sha256": bipgen.graph_sha256(g), "counts_per_step": len(pqs),
+            "anchor": {str(k): _auto_anchor(g, k) for k in pqs},
+            "l2": "512 MiB written between timed steps (outside the events); per-count "
+                  "scratch also exceeds L2",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
 def reference_arm(args, pqs):
-    """The oracle timed on this host's cores, each step a bounded sample."""
+    """The oracle on this host's cores.  Each step times the same fixed sample of
+    roots of every count (stored with the oracle's full run) and scales the full
+    run's core-seconds by the ratio of the two timings of those roots; the value
+    is the resulting time per whole count on all host cores, and ms_per_step is
+    the measured wall time of the step (the sample)."""
     g = bipgen.workload_powerlaw_2m()
-    anchors = [_auto_anchor(g, k) for k in pqs]
-    times = []
-    detail = []
-    budget = min(args.cpu_budget, 12.0)
     cores = host_cores()
+    orc = OracleSample("powerlaw2m", "workload_powerlaw_2m", [(k, k) for k in pqs], cores)
     for _ in range(args.warmup):
-        oracle_sample(pqs[:1], anchors[:1], 1.0, seed=3, workers=cores)
-    for s in range(args.steps):
-        est_s, detail = oracle_sample(pqs, anchors, budget, seed=11 + s, workers=cores)
-        times.append(est_s * 1e3 / len(pqs))
-    v = statistics.mean(times)
+        orc.run()
+    walls, values, detail = [], [], []
+    for _ in range(args.steps):
+        wall, est, detail = orc.run()
+        walls.append(wall)
+        values.append(1e3 * statistics.mean(est[(k, k)] for k in pqs if (k, k) in est))
+    orc.close()
+    v = statistics.mean(values)
+    sample = (f"per step: the fixed sample of {len(orc.tasks)} roots (the same every step, drawn with probability "
+              f"proportional to their time in the stored full oracle run) timed on {cores} processes; each whole "
+              f"count = stored full-run core-seconds x (time here / stored time of the same roots) / cores; "
+              f"steps' values range {min(values):.0f}..{max(values):.0f} ms; " + "; ".join(detail)
+              + ("; no stored full run for " + str(orc.missing) if orc.missing else ""))
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * len(pqs), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u128 (CPU oracle)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "counts_per_step": len(pqs)},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": "per step: seeded uniform sample of roots per (p,q) shared by one oracle "
-                                   "process per host core, scaled to all roots; " + "; ".join(detail)},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(walls),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u128 (CPU oracle)",
+        "data": "synthetic", "config": sweep_config(g, pqs),
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)

@@ -2,13 +2,17 @@
 (Chung-Lu seed 2, 200k x 100k, exponents 2.0 / 2.3) with the p = q = 2..6
 counts the benchmark times, each through the anchor the library picks.
 
-The oracle cannot walk every tree here (10^12 leaves at p = q = 5), so the GPU
-is checked by sampled per-root counts against the oracle, one root at a time,
-and, for p = q >= 4, by agreement of the two anchors, whose search trees share
-nothing.  Roots are sampled uniformly from those of at most 64 neighbours (most
-of them; the oracle walks each in well under a second), plus three of 65 to 128
-neighbours, whose trees are deep at p = q = 5 and 6 (a second or two of oracle
-time each), plus, for p = q <= 4, the largest roots of at most 64 neighbours."""
+The oracle counted every one of these to completion on the host's cores
+(tests/golden/oracle_full_counts.py, all roots, exact per-root values): the
+GPU's whole count must equal the oracle's, its whole per-root vector must have
+the same SHA-256, and the 50 roots the oracle took longest on (the hubs that
+hold most of the work) must match value by value.  A fast sampled check of
+light roots against the oracle, one root at a time, stays beside it, and the
+two anchors (trees that share nothing) must agree."""
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -17,10 +21,43 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
+FULL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_counts.json")
+
 
 @pytest.fixture(scope="module")
 def powerlaw():
     return bipgen.workload_powerlaw_2m()
+
+
+@pytest.fixture(scope="module")
+def stored(powerlaw):
+    rec = json.load(open(FULL))["powerlaw2m"]
+    assert rec["sha256"] == bipgen.graph_sha256(powerlaw)
+    return rec["counts"]
+
+
+def _sha(values):
+    h = hashlib.sha256()
+    for v in values:
+        h.update(f"{int(v)}\n".encode())
+    return h.hexdigest()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
+def test_whole_counts_equal_the_oracle(gpu_ctx, powerlaw, stored, k):
+    res = stored.get(f"{k},{k}")
+    if res is None or "count" not in res:
+        pytest.skip(f"no whole oracle count stored for p=q={k}: {res.get('unavailable') if res else 'not run'}")
+    h = gpu_ctx.load(powerlaw)
+    total, info = h.count_ex(k, k)
+    assert info["anchor"] == res["anchor"]
+    assert total == int(res["count"])
+    tot, per = h.count_per_root(k, k, res["anchor"])
+    assert tot == total
+    for hr in res["heaviest_roots"]:
+        assert per[hr["root"]] == int(hr["value"]), (k, hr["root"])
+    assert _sha(per) == res["per_root_sha256"]
+    h.close()
 
 
 @pytest.mark.parametrize("k,n_sample", [(2, 24), (3, 24), (4, 16), (5, 12), (6, 8)])
@@ -37,8 +74,6 @@ def test_sampled_roots_match_the_oracle(gpu_ctx, powerlaw, k, n_sample):
     sample = [int(x) for x in rng.choice(light, n_sample, replace=False)]
     mid = np.flatnonzero((deg > 64) & (deg <= 128))
     sample += [int(x) for x in rng.choice(mid, 3, replace=False)]
-    if k <= 4:
-        sample += [int(x) for x in light[np.argsort(deg[light])[-3:]]]
     for r in sample:
         assert per[r] == oracle.count(g, k, k, anchor=anchor, roots=(r, r + 1)), (k, anchor, r)
     h.close()
