@@ -53,9 +53,10 @@ def _args():
                     help="skip the dense-core timings and the batched-vs-plain comparison of the default line")
     ap.add_argument("--no-roofline", action="store_true",
                     help="skip the untimed statistics pass and microbenchmarks behind the roofline")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "ablation"],
                     help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain; "
-                         "serve: Poisson query stream over 8 resident graphs")
+                         "serve: Poisson query stream over 8 resident graphs; ablation: bitmap vs sorted-list "
+                         "(CSR) sets on the 2M-edge and dense-core graphs")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="size factor of the serving graphs (1 = stated)")
     ap.add_argument("--serve-limit-ms", type=int, default=30_000, help="per-request device deadline when serving")
     ap.add_argument("--serve-per-rate", type=int, default=120, help="queries per arrival rate")
@@ -228,6 +229,9 @@ def main():
         return
     if args.workload == "serve":
         serve_workload(args, rank, world, local)
+        return
+    if args.workload == "ablation":
+        ablation_workload(args, local)
         return
 
     # host-side inputs first: process pools are spawned before CUDA starts
@@ -475,11 +479,47 @@ def batch_comparison(ctx, jobs, flush, reps=3):
 
     t_batch = timed(lambda: ctx.count_batch(hs, ps, qs))
     t_plain = timed(lambda: [h.count(p, q) for h, p, q in zip(hs, ps, qs)])
+    # where the time goes: each job alone (plain), and the comparison again
+    # without the ten longest jobs
+    alone = []
+    for i, (h, p, q) in enumerate(zip(hs, ps, qs)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.count(p, q)
+        torch.cuda.synchronize()
+        alone.append((time.perf_counter() - t0, i))
+    alone.sort(reverse=True)
+    rest = sorted(i for _, i in alone[10:])
+    sub = ([hs[i] for i in rest], [ps[i] for i in rest], [qs[i] for i in rest])
+    ref_rest = [ref[i] for i in rest]
+
+    def timed_rest(fn):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fn()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+            assert res == ref_rest
+        return statistics.mean(out)
+
+    tb_rest = timed_rest(lambda: ctx.count_batch(*sub))
+    tp_rest = timed_rest(lambda: [h.count(p, q) for h, p, q in zip(*sub)])
+    total_alone = sum(t for t, _ in alone)
+    top = alone[0][1]
+    tuned_warps = sum(1 for h, p, q in zip(hs, ps, qs) if h.tuned_warps(p, q))
     for h in hs:
         h.close()
     return {"workload": BATCH_WORKLOAD, "queries": len(jobs), "reps": reps,
             "batched_qps": len(jobs) / t_batch, "plain_qps": len(jobs) / t_plain,
             "batched_over_plain": t_plain / t_batch, "identical_counts": True,
+            "largest_job": {"p": ps[top], "q": qs[top], "edges": int(jobs[top][0].n_edges),
+                            "share_of_plain": alone[0][0] / total_alone},
+            "ten_largest_share_of_plain": sum(t for t, _ in alone[:10]) / total_alone,
+            "without_ten_largest": {"queries": len(rest), "batched_qps": len(rest) / tb_rest,
+                                    "plain_qps": len(rest) / tp_rest, "batched_over_plain": tp_rest / tb_rest},
+            "autotuned_warps_kept": tuned_warps,
             "how": "host wall clock around each pass (synchronised), graphs resident"}
 
 
@@ -675,6 +715,53 @@ def serve_workload(args, rank, world, local):
     for h in hs:
         h.close()
     ctx.close()
+
+
+def ablation_workload(args, local, limit_ms=60_000):
+    """Device time of the same counts with bitmap sets (the library's kernels)
+    and with sorted-list sets intersected by binary search (the CSR
+    representation of Sec. III-B), same search trees, graph resident: one
+    untimed count, then `steps` timed counts each (the CSR counts stop at
+    limit_ms)."""
+    import torch
+    import paper_2403_07858_gb300 as gbc
+    torch.cuda.set_device(local)
+    gbc.build()
+    ctx = gbc.Context(local)
+    rows = []
+    for name, g, pairs in [("chung-lu seed 2, 200k x 100k, 2M edges", bipgen.workload_powerlaw_2m(),
+                            [(3, 3), (4, 4), (5, 5), (6, 6)]),
+                           ("dense core, 50k x 50k ER 5M edges + 20 planted K_{40,40}", bipgen.workload_dense_core(),
+                            DENSE_PAIRS)]:
+        h = ctx.load(g)
+        for p, q in pairs:
+            n, info = h.count_ex(p, q)
+            row = {"graph": name, "p": p, "q": q, "anchor": info["anchor"], "count": str(n)}
+            for kern in ("bitmap", "csr"):
+                ms, ok = [], True
+                for rep in range(1 + max(1, args.steps)):
+                    try:
+                        m, inf = h.count_ex(p, q, anchor=info["anchor"], kernel=kern,
+                                            time_limit_ms=limit_ms if kern == "csr" else 0)
+                    except gbc.CountTimeout:
+                        ok = False
+                        break
+                    assert m == n
+                    if rep:
+                        ms.append((inf["ms_total"], inf["ms_enumerate"]))
+                row[kern] = ({"ms_total": statistics.mean(a for a, _ in ms),
+                              "ms_enumerate": statistics.mean(b for _, b in ms)} if ok
+                             else {"over_limit_ms": limit_ms})
+            if "ms_total" in row["csr"]:
+                row["csr_over_bitmap"] = row["csr"]["ms_total"] / row["bitmap"]["ms_total"]
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        h.close()
+    ctx.close()
+    print(json.dumps({"metric": "time per (p,q) count, bitmap vs sorted-list (CSR) sets", "unit": "ms",
+                      "steps": args.steps, "rows": rows,
+                      "how": "device time (CUDA events on the library's stream) of gbc_count_ex with "
+                             "kernel = bitmap and kernel = csr, the same anchor and search tree"}), flush=True)
 
 
 def kernel_source_digest() -> str:

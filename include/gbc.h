@@ -132,8 +132,15 @@ typedef struct {
                             anchor vertex lies there (Def. 2 reading); disjoint ranges that cover
                             the anchor side add up to the count (the split used across GPUs) */
     int32_t root_end;
-    int32_t reserved[2];
+    int32_t kernel;      /* GBC_KERNEL_BITMAP (0, the default) or GBC_KERNEL_CSR: the same search trees
+                            with sorted neighbour lists intersected by binary search instead of
+                            bitmaps (the CSR representation Sec. III-B describes; an ablation, counts
+                            with |L| >= 3 on the anchor side only) */
+    int32_t reserved;
 } gbc_count_options;
+
+/* Set representation of the enumeration (gbc_count_options.kernel). */
+enum { GBC_KERNEL_BITMAP = 0, GBC_KERNEL_CSR = 1 };
 
 /* Facts about one count (host output of gbc_count_ex). */
 typedef struct {
@@ -259,8 +266,9 @@ gbc_status gbc_count_batch(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, cons
  * gbc_autotune -- for each job (graphs[i], p[i], q[i]) with p, q >= 2, count it
  * from both anchor sides (each run bounded by time_limit_ms, the second also by
  * 1.2x the first's time), check that both agree, and remember the faster side
- * in the context.  Later gbc_count / gbc_count_batch calls on the same (graph,
- * p, q) use it (an explicit anchor option still wins).  The layer choice is a
+ * in the context; for |L| >= 4 it then times the enumeration with fewer warps
+ * (gbc_tuned_warps).  Later gbc_count / gbc_count_batch calls on the same
+ * (graph, p, q) use both (explicit options still win).  The layer choice is a
  * cost question the paper leaves to its CPU predecessor (Sec. IV); this
  * measures it instead.  Entries are dropped when their graph is freed.
  * Errors: GBC_ERR_ARG, and the errors of gbc_count except GBC_ERR_TIMEOUT.
@@ -270,6 +278,13 @@ gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *graphs, const i
 
 /* The anchor gbc_autotune chose for (g, p, q): GBC_ANCHOR_U, GBC_ANCHOR_V, or 0 if untuned. */
 int gbc_tuned_anchor(gbc_graph_t g, int p, int q);
+
+/* The enumeration warps gbc_autotune kept for (g, p, q), or 0 (the default:
+ * every SM filled to its occupancy; the autotuner also times a half and a
+ * quarter of the SMs' 32 warps each and keeps one only if it is >= 3% faster).
+ * A launch over several counts uses the tuned warps only when all of them
+ * have some (their largest). */
+int gbc_tuned_warps(gbc_graph_t g, int p, int q);
 
 /*
  * Serving (continuous batching).  gbc_serve_start starts `workers` threads

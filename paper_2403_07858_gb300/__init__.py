@@ -61,7 +61,7 @@ class CountOptions(ctypes.Structure):
     _fields_ = [("anchor", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("enum_warps", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32),
                 ("root_begin", ctypes.c_int32), ("root_end", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class CountInfo(ctypes.Structure):
@@ -134,6 +134,7 @@ SIGNATURES = {
     "gbc_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "gbc_tuned_anchor": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "gbc_tuned_warps": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "gbc_serve_start": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gbc_serve_stop": (ctypes.c_int, [_vp]),
     "gbc_serve_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(ServeStats)]),
@@ -235,10 +236,12 @@ class Graph:
 
     def count_ex(self, p: int, q: int, anchor: str = "auto", stats: bool = False,
                  enum_warps: int = 0, time_limit_ms: int = 0,
-                 roots: tuple[int, int] | None = None) -> tuple[int, dict]:
+                 roots: tuple[int, int] | None = None, kernel: str = "bitmap") -> tuple[int, dict]:
         """roots: count only the search trees rooted in this half-open range of
-        anchor vertices (give the anchor explicitly when splitting a count)."""
+        anchor vertices (give the anchor explicitly when splitting a count).
+        kernel: "bitmap" (the default) or "csr" (the sorted-list ablation)."""
         opt = CountOptions()
+        opt.kernel = {"bitmap": 0, "csr": 1}[kernel]
         opt.anchor = ANCHORS[anchor]
         opt.collect_stats = 1 if stats else 0
         opt.enum_warps = enum_warps
@@ -291,6 +294,10 @@ class Graph:
 
     def tuned_anchor(self, p: int, q: int) -> str | None:
         return _ANCHOR_NAMES.get(load_library().gbc_tuned_anchor(self._h, p, q))
+
+    def tuned_warps(self, p: int, q: int) -> int:
+        """Enumeration warps the autotuner kept for (p, q); 0 = the default."""
+        return int(load_library().gbc_tuned_warps(self._h, p, q))
 
     def count_per_root(self, p: int, q: int, anchor: str) -> tuple[int, list[int]]:
         n_a = self.n_u if anchor == "U" else self.n_v

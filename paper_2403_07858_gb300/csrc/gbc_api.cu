@@ -122,6 +122,7 @@ struct gbc_ctx_s {
     Lane lane;                               // the lane of the synchronous calls
     std::mutex tune_mu;
     std::map<TuneKey, int> tuned_anchor;     // filled by gbc_autotune
+    std::map<TuneKey, int> tuned_warps;      // enumeration warps gbc_autotune measured faster than the default
     std::map<FootKey, size_t> footprint;     // exact scratch bytes of counts that ran (tune_mu)
     std::mutex mu;
     int live_graphs = 0;
@@ -247,6 +248,8 @@ void gbc_free_graph(gbc_graph_t g) {
             it = it->first.graph == g ? g->ctx->tuned_anchor.erase(it) : std::next(it);
         for (auto it = g->ctx->footprint.begin(); it != g->ctx->footprint.end();)
             it = it->first.graph == g ? g->ctx->footprint.erase(it) : std::next(it);
+        for (auto it = g->ctx->tuned_warps.begin(); it != g->ctx->tuned_warps.end();)
+            it = it->first.graph == g ? g->ctx->tuned_warps.erase(it) : std::next(it);
     }
     delete g;
 }
@@ -867,6 +870,21 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         todo.push_back(i);
     }
     auto need_of = [&](int i) { return wave_need(jobs[i].a.k, hs[i].totals, jobs[i].g->nE); };
+    const bool csr = opt && opt->kernel == GBC_KERNEL_CSR;
+    // enumeration warps of a launch over `ids`: the option, else the tuned warps
+    // of its jobs when every one of them has some (their largest), else 0 (auto)
+    auto warps_for = [&](const std::vector<int> &ids) -> int {
+        if (opt && opt->enum_warps > 0) return opt->enum_warps;
+        std::lock_guard<std::mutex> lk(ctx->tune_mu);
+        int w = 0;
+        for (int i : ids) {
+            if (jobs[i].a.k < 4) continue;
+            auto it = ctx->tuned_warps.find(TuneKey{jobs[i].g, jobs[i].p, jobs[i].q});
+            if (it == ctx->tuned_warps.end()) return 0;
+            w = std::max(w, it->second);
+        }
+        return w;
+    };
     std::vector<char> in_todo(n, 0);
     for (int i : todo) in_todo[i] = 1;
     // exact footprint of each job that got through the scans (serving admission)
@@ -887,6 +905,10 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     // Sec. VI, applied to the scratch; the graph itself stays resident).
     auto run_in_pieces = [&](int i, size_t avail) -> gbc_status {
         Job &J = jobs[i];
+        if (opt && opt->kernel == GBC_KERNEL_CSR) {
+            J.set_error(GBC_ERR_OOM, "gbc_count: the sorted-list ablation runs whole; its scratch exceeds the budget");
+            return GBC_OK;
+        }
         const CountArgs &a = J.a;
         const int64_t nA = a.g.nA;
         const bool k4 = a.k >= 4;
@@ -975,7 +997,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                 CK(cudaMemsetAsync(d_queue, 0, 4, st));
                 CK(cudaMemcpyAsync(d_job, &b, sizeof(CountArgs), cudaMemcpyHostToDevice, st));
                 CK(launch_sort_units(u_all, u_bucket, ucnt, ucnt + 1, ucnt + 17, u_sorted, nc, st));
-                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, want_stats, opt ? opt->enum_warps : 0,
+                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, want_stats, warps_for(std::vector<int>{i}),
                                     (int)row_stride(a.g.maxdegA), (std::max(hs[i].cand_max, 1) + 31) / 32, a.k,
                                     ctx->n_sms, st));
             }
@@ -1133,6 +1155,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             CountArgs &a = jobs[i].a;
             const Small &h = hs[i];
             if (a.k >= 4) a.job_id = (int32_t)enum_jobs.size();
+            if (csr) continue;
             CK(launch_pairs(a, ctx->n_sms, sj(i)));
             if (a.k >= 4) {
                 enum_jobs.push_back(a);
@@ -1143,6 +1166,25 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         }
         CK(join());
         tm.mark(2, st);
+        if (csr) {
+            // the sorted-list ablation walks the same trees from pass B's candidate lists
+            for (int i : wave) {
+                CountArgs &a = jobs[i].a;
+                CsrArgs C;
+                memset(&C, 0, sizeof C);
+                C.dmax = std::max(a.g.maxdegA, 1);
+                C.cmax = std::max(hs[i].cand_max, 1);
+                C.stack_words = csr_stack_words(a.k, C.dmax, C.cmax);
+                const int warps = (int)std::max<int64_t>(
+                    1, std::min<int64_t>((int64_t)ctx->n_sms * 32, (int64_t(1) << 28) / C.stack_words));
+                CK(wave_sc.get(&C.queue, 1));
+                CK(cudaMemsetAsync(C.queue, 0, 4, st));
+                CK(wave_sc.get(&C.stack, (size_t)warps * C.stack_words));
+                CK(launch_enumerate_csr(a, C, warps, want_stats, st));
+            }
+            CK(cudaStreamSynchronize(st));
+            enum_jobs.clear();
+        }
         if (!enum_jobs.empty()) {
             CountArgs *d_jobs = nullptr;
             int32_t *d_queue = nullptr;
@@ -1153,7 +1195,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                                cudaMemcpyHostToDevice, st));
             CK(launch_sort_units(units_all, units_bucket, ucounters, ucounters + 1, ucounters + 17, units_sorted,
                                  unit_cap, st));
-            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, want_stats, opt ? opt->enum_warps : 0,
+            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, want_stats, warps_for(wave),
                                 max_wr, max_wl, max_k, ctx->n_sms, st));
             // the job table is read by the launch: keep the host copy alive until it has run
             if (on_done) CK(wait_releasing(wave));
@@ -1204,6 +1246,8 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
     CK(cudaSetDevice(ctx->device));
     const int anchor = resolve_anchor(g, p, q, force_anchor ? force_anchor : (opt ? opt->anchor : 0));
     if (anchor != GBC_ANCHOR_U && anchor != GBC_ANCHOR_V) return fail(GBC_ERR_ARG, "gbc_count: bad anchor %d", anchor);
+    if (opt && (opt->kernel < GBC_KERNEL_BITMAP || opt->kernel > GBC_KERNEL_CSR))
+        return fail(GBC_ERR_ARG, "gbc_count: bad kernel %d", opt->kernel);
     const bool want_stats = opt && opt->collect_stats;
     std::vector<Job> jobs(1);
     jobs[0].g = g;
@@ -1475,10 +1519,49 @@ extern "C" gbc_status gbc_autotune(gbc_ctx_t ctx, int n, const gbc_graph_t *grap
         const float t2 = s2 == GBC_OK ? info.ms_total : 1e30f;
         if (s1 == GBC_OK && s2 == GBC_OK && (v1.lo != v2.lo || v1.hi != v2.hi))
             return fail(GBC_ERR_CUDA, "gbc_autotune: the two anchors disagree on (%d,%d)", p[i], q[i]);
-        std::lock_guard<std::mutex> lk(ctx->tune_mu);
-        ctx->tuned_anchor[key] = t2 < t1 ? second : first;
+        const int best = t2 < t1 ? second : first;
+        const float t_best = std::min(t1, t2);
+        {
+            std::lock_guard<std::mutex> lk(ctx->tune_mu);
+            ctx->tuned_anchor[key] = best;
+        }
+        // warps of the persistent enumeration launch: the default fills every SM
+        // to its occupancy; fewer warps are kept only if they are >= 3% faster
+        const int k = best == GBC_ANCHOR_U ? p[i] : q[i];
+        if (k >= 4 && t_best < 1e29f) {
+            o.anchor = best;
+            float t_w = t_best;
+            int w_best = 0;
+            for (int frac : {2, 4}) {
+                o.enum_warps = ctx->n_sms * 32 / frac;
+                o.time_limit_ms = std::max(1, (int)(t_best * 1.2f) + 1);
+                gbc_u128 v3;
+                const gbc_status s3 = count_impl(graphs[i], p[i], q[i], &o, &v3, &info, 0, nullptr);
+                if (s3 == GBC_ERR_TIMEOUT) continue;
+                if (s3 != GBC_OK) return s3;
+                const gbc_u128 &vb = best == first ? v1 : v2;
+                if (v3.lo != vb.lo || v3.hi != vb.hi)
+                    return fail(GBC_ERR_CUDA, "gbc_autotune: warp counts disagree on (%d,%d)", p[i], q[i]);
+                if (info.ms_total < 0.97f * t_w) {
+                    t_w = info.ms_total;
+                    w_best = o.enum_warps;
+                }
+            }
+            o.enum_warps = 0;
+            if (w_best > 0) {
+                std::lock_guard<std::mutex> lk(ctx->tune_mu);
+                ctx->tuned_warps[key] = w_best;
+            }
+        }
     }
     return GBC_OK;
+}
+
+extern "C" int gbc_tuned_warps(gbc_graph_t g, int p, int q) {
+    if (!g) return 0;
+    std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
+    auto it = g->ctx->tuned_warps.find(TuneKey{g, p, q});
+    return it == g->ctx->tuned_warps.end() ? 0 : it->second;
 }
 
 extern "C" int gbc_tuned_anchor(gbc_graph_t g, int p, int q) {

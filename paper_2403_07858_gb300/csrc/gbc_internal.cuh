@@ -284,6 +284,18 @@ struct ListArgs {
 int64_t list_stack_words(int k, int32_t maxdeg, int64_t cand_max);
 cudaError_t launch_list(const CountArgs &a, const ListArgs &L, int warps, cudaStream_t st);
 
+// The sorted-list (CSR) ablation of the enumeration (gbc_csr.cu): warp per
+// root over [lib_begin, lib_end), per-warp stacks of k * (dmax + cmax) ints.
+struct CsrArgs {
+    int32_t *queue;          // zeroed work counter
+    int32_t *stack;          // per-warp depth-first stacks
+    int64_t stack_words;     // ints of one warp's stack
+    int32_t dmax;            // largest anchor degree (C_R capacity per level)
+    int64_t cmax;            // largest candidate list (C_L capacity per level)
+};
+int64_t csr_stack_words(int k, int32_t dmax, int64_t cmax);
+cudaError_t launch_enumerate_csr(const CountArgs &a, const CsrArgs &C, int warps, bool stats, cudaStream_t st);
+
 // Launchers (gbc_kernels.cu).  All run on `st`; none synchronises.
 cudaError_t launch_validate_offsets(const int32_t *off, int32_t n, int64_t nE, uint32_t *status, cudaStream_t st);
 cudaError_t launch_validate_rows(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other,
