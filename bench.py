@@ -53,10 +53,11 @@ def _args():
                     help="skip the dense-core timings and the batched-vs-plain comparison of the default line")
     ap.add_argument("--no-roofline", action="store_true",
                     help="skip the untimed statistics pass and microbenchmarks behind the roofline")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "ablation"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "batch", "serve", "ablation", "border"],
                     help="sweep: p=q in 2..6 on the 2M-edge graph; batch: 256 graphs, batched vs plain; "
                          "serve: Poisson query stream over 8 resident graphs; ablation: bitmap vs sorted-list "
-                         "(CSR) sets on the 2M-edge and dense-core graphs")
+                         "(CSR) sets on the 2M-edge and dense-core graphs; border: the per-root position "
+                         "orders (most shared first, degree order, Border's order) on the 2M-edge graph")
     ap.add_argument("--serve-scale", type=float, default=1.0, help="size factor of the serving graphs (1 = stated)")
     ap.add_argument("--serve-limit-ms", type=int, default=30_000, help="per-request device deadline when serving")
     ap.add_argument("--serve-per-rate", type=int, default=120, help="queries per arrival rate")
@@ -232,6 +233,9 @@ def main():
         return
     if args.workload == "ablation":
         ablation_workload(args, local)
+        return
+    if args.workload == "border":
+        border_workload(args, local)
         return
 
     # host-side inputs first: process pools are spawned before CUDA starts
@@ -762,6 +766,77 @@ def ablation_workload(args, local, limit_ms=60_000):
                       "steps": args.steps, "rows": rows,
                       "how": "device time (CUDA events on the library's stream) of gbc_count_ex with "
                              "kernel = bitmap and kernel = csr, the same anchor and search tree"}), flush=True)
+
+
+def _relabel(g, new_u, new_v):
+    """g with vertex u of U renamed new_u[u] and v of V renamed new_v[v]."""
+    import numpy as np
+    us = np.repeat(np.arange(g.n_u), np.diff(g.off_u))
+    return bipgen.from_edges(g.n_u, g.n_v, np.asarray(new_u)[us], np.asarray(new_v)[np.asarray(g.adj_u)])
+
+
+def border_workload(args, local, iterations=20_000):
+    """Bit order of the per-root C_R bitmaps on the 2M-edge graph (Sec. V-B):
+    most shared position first (the library's default), the other side's
+    degree order, and Border's order of the other side.  For the last two the
+    anchor side is renumbered by degree, the other side by degree or by
+    gbc_border_order, and the graph is loaded with its ids kept.  Reports the
+    enumeration's device time and the C_R words it loads per evaluated child
+    (its span-truncated reads, from a statistics pass)."""
+    import numpy as np
+    import torch
+    import paper_2403_07858_gb300 as gbc
+    torch.cuda.set_device(local)
+    gbc.build()
+    g = bipgen.workload_powerlaw_2m()
+
+    def degree_ids(off):
+        deg = np.diff(off)
+        order = np.argsort(-deg, kind="stable")
+        ids = np.empty(len(deg), dtype=np.int64)
+        ids[order] = np.arange(len(deg))
+        return ids
+
+    ctx = gbc.Context(local)
+    rows = []
+    for k, anchor in [(4, "U"), (5, "V"), (6, "V")]:
+        if anchor == "U":
+            a_ids = degree_ids(g.off_u)
+            nA, nO, off, adj = g.n_u, g.n_v, g.off_u, g.adj_u
+        else:
+            a_ids = degree_ids(g.off_v)
+            nA, nO, off, adj = g.n_v, g.n_u, g.off_v, g.adj_v
+        t0 = time.perf_counter()
+        border_ids, ob_before, ob_after = gbc.border_order(nA, nO, off, adj, iterations=iterations, max_cand=64)
+        t_border = time.perf_counter() - t0
+        deg_ids, _, _ = gbc.border_order(nA, nO, off, adj, iterations=0, max_cand=64)
+        variants = [("most shared first (default)", g, False, "shared")]
+        for name, o_ids in [("other side's degree order", deg_ids), ("Border's order", border_ids)]:
+            gg = _relabel(g, a_ids, o_ids) if anchor == "U" else _relabel(g, o_ids, a_ids)
+            variants.append((name, gg, True, "id"))
+        want = None
+        for name, gg, keep, order in variants:
+            h = ctx.load(gg, keep_ids=keep)
+            n, info = h.count_ex(k, k, anchor=anchor, position_order=order)
+            want = n if want is None else want
+            assert n == want
+            ms = []
+            for _ in range(max(1, args.steps)):
+                _, inf = h.count_ex(k, k, anchor=anchor, position_order=order)
+                ms.append(inf["ms_enumerate"])
+            _, st = h.count_ex(k, k, anchor=anchor, position_order=order, stats=True)
+            evals = sum(st["evals"][3:])
+            rows.append({"p": k, "q": k, "anchor": anchor, "order": name, "ms_enumerate": statistics.mean(ms),
+                         "loaded_words": st["enum_words"], "evaluated_children": evals,
+                         "words_per_child": st["enum_words"] / max(1, evals), "count": str(n)})
+            print(json.dumps(rows[-1]), flush=True)
+            h.close()
+        rows.append({"p": k, "q": k, "anchor": anchor, "border_iterations": iterations,
+                     "one_blocks_degree_order": ob_before, "one_blocks_border": ob_after, "border_s": t_border})
+        print(json.dumps(rows[-1]), flush=True)
+    ctx.close()
+    print(json.dumps({"metric": "enumeration time and C_R words per evaluated child by position order",
+                      "graph": WORKLOAD, "steps": args.steps, "rows": rows}), flush=True)
 
 
 def kernel_source_digest() -> str:

@@ -98,6 +98,16 @@ gbc_status gbc_load_graph(gbc_ctx_t ctx, int32_t nU, int32_t nV,
                           const int32_t *offV, const int32_t *adjV,
                           gbc_graph_t *out);
 
+/* As gbc_load_graph (host arrays), with flags: GBC_LOAD_KEEP_IDS keeps the
+ * caller's vertex ids on the device instead of renumbering each side by degree
+ * (the counts are the same; the other side's id order is then the caller's,
+ * e.g. an order from gbc_border_order). */
+#define GBC_LOAD_KEEP_IDS 1
+gbc_status gbc_load_graph_ex(gbc_ctx_t ctx, int32_t nU, int32_t nV,
+                             const int32_t *offU, const int32_t *adjU,
+                             const int32_t *offV, const int32_t *adjV,
+                             int32_t flags, gbc_graph_t *out);
+
 /* As gbc_load_graph, but the four arrays are device pointers (borrowed; the
  * graph keeps its own copy).  The renumbering copies the U side's arrays and
  * V's offsets to the host once. */
@@ -136,7 +146,10 @@ typedef struct {
                             with sorted neighbour lists intersected by binary search instead of
                             bitmaps (the CSR representation Sec. III-B describes; an ablation, counts
                             with |L| >= 3 on the anchor side only) */
-    int32_t reserved;
+    int32_t position_order; /* bit order of a root's C_R bitmaps over the positions of N(u):
+                               0 = most shared position first (the default), 1 = the other side's
+                               id order (on a graph relabelled by gbc_border_order: Border's order,
+                               Sec. V-B); the count does not depend on it */
 } gbc_count_options;
 
 /* Set representation of the enumeration (gbc_count_options.kernel). */
@@ -348,6 +361,25 @@ gbc_status gbc_submit(gbc_ctx_t ctx, gbc_graph_t g, int p, int q, uint64_t *tick
  * retired.  Errors: GBC_ERR_ARG (unknown ticket, not serving) and the count's.
  */
 gbc_status gbc_poll(gbc_ctx_t ctx, uint64_t ticket, int timeout_ms, gbc_u128 *out);
+
+/*
+ * gbc_border_order -- Border (Sec. V-B, Alg. 2), host preprocessing: a new id
+ * order of side O that lowers the number of 1-blocks (32-id blocks holding a
+ * single neighbour) in the adjacency rows of side A, starting from the order
+ * by descending degree and taking at most `iterations` greedy exchanges.
+ *   nA, offA [nA+1], adjA [|E|]: A -> O CSR (host, borrowed), nO columns;
+ *   max_cand: candidates whose exchange profit each iteration evaluates (the
+ *     least-overlapping columns in the blocks v_m's rows fill most; >= 1);
+ *   new_id [nO] (host output): the new id of every O vertex (a permutation);
+ *   one_blocks_before / _after (host, may be NULL): 1-blocks of the degree
+ *     order and of the result.
+ * The library's bitmaps are per root over positions of N(u), so Border's order
+ * reaches them only through gbc_count_options.position_order = 1 on a graph
+ * relabelled with it.  Errors: GBC_ERR_ARG.
+ */
+gbc_status gbc_border_order(int32_t nA, int32_t nO, const int32_t *offA, const int32_t *adjA,
+                            int32_t iterations, int32_t max_cand, int32_t *new_id,
+                            int64_t *one_blocks_before, int64_t *one_blocks_after);
 
 /*
  * gbc_measure_int_peaks -- two microbenchmarks on `device` that scale the

@@ -61,7 +61,7 @@ class CountOptions(ctypes.Structure):
     _fields_ = [("anchor", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("enum_warps", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32),
                 ("root_begin", ctypes.c_int32), ("root_end", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("position_order", ctypes.c_int32)]
 
 
 class CountInfo(ctypes.Structure):
@@ -119,6 +119,7 @@ SIGNATURES = {
     "gbc_ctx_destroy": (None, [_vp]),
     "gbc_load_graph": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "gbc_load_graph_device": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "gbc_load_graph_ex": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_vp)]),
     "gbc_free_graph": (None, [_vp]),
     "gbc_graph_info": (ctypes.c_int, [_vp, _i32p, _i32p, ctypes.POINTER(_i64), _i32p, _i32p]),
     "gbc_count": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128)]),
@@ -147,6 +148,8 @@ SIGNATURES = {
     "gbc_list_end": (None, [_vp]),
     "gbc_submit": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "gbc_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(U128)]),
+    "gbc_border_order": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _i32, _vp, ctypes.POINTER(_i64),
+                                        ctypes.POINTER(_i64)]),
     "gbc_measure_int_peaks": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double)]),
     "gbc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -236,12 +239,16 @@ class Graph:
 
     def count_ex(self, p: int, q: int, anchor: str = "auto", stats: bool = False,
                  enum_warps: int = 0, time_limit_ms: int = 0,
-                 roots: tuple[int, int] | None = None, kernel: str = "bitmap") -> tuple[int, dict]:
+                 roots: tuple[int, int] | None = None, kernel: str = "bitmap",
+                 position_order: str = "shared") -> tuple[int, dict]:
         """roots: count only the search trees rooted in this half-open range of
         anchor vertices (give the anchor explicitly when splitting a count).
-        kernel: "bitmap" (the default) or "csr" (the sorted-list ablation)."""
+        kernel: "bitmap" (the default) or "csr" (the sorted-list ablation).
+        position_order: "shared" (most shared position first, the default) or
+        "id" (the other side's id order)."""
         opt = CountOptions()
         opt.kernel = {"bitmap": 0, "csr": 1}[kernel]
+        opt.position_order = {"shared": 0, "id": 1}[position_order]
         opt.anchor = ANCHORS[anchor]
         opt.collect_stats = 1 if stats else 0
         opt.enum_warps = enum_warps
@@ -334,10 +341,17 @@ class Context:
             lib.gbc_ctx_destroy(self._h)
             self._h = ctypes.c_void_p()
 
-    def load_graph(self, n_u: int, n_v: int, off_u, adj_u, off_v, adj_v) -> Graph:
+    def load_graph(self, n_u: int, n_v: int, off_u, adj_u, off_v, adj_v, keep_ids: bool = False) -> Graph:
+        """keep_ids: keep the caller's vertex ids on the device (host arrays only)
+        instead of renumbering each side by degree; the counts are the same."""
         lib = load_library()
         h = ctypes.c_void_p()
         arrays = (off_u, adj_u, off_v, adj_v)
+        if keep_ids:
+            keep = [_ptr_host(x) for x in arrays]
+            ptrs = [ctypes.c_void_p(p) for _, p in keep]
+            _check(lib.gbc_load_graph_ex(self._h, n_u, n_v, *ptrs, 1, ctypes.byref(h)), "gbc_load_graph_ex")
+            return Graph(self, h.value)
         if all(_is_cuda_tensor(x) for x in arrays):
             ptrs = [ctypes.c_void_p(x.data_ptr()) for x in arrays]
             _check(lib.gbc_load_graph_device(self._h, n_u, n_v, *ptrs, ctypes.byref(h)), "gbc_load_graph_device")
@@ -400,9 +414,9 @@ class Context:
         _check(s, "gbc_poll")
         return out.value()
 
-    def load(self, g) -> Graph:
+    def load(self, g, keep_ids: bool = False) -> Graph:
         """Load a ``bipgen.BipartiteGraph`` (or anything with the same fields)."""
-        return self.load_graph(g.n_u, g.n_v, g.off_u, g.adj_u, g.off_v, g.adj_v)
+        return self.load_graph(g.n_u, g.n_v, g.off_u, g.adj_u, g.off_v, g.adj_v, keep_ids=keep_ids)
 
 
 def count_p2_noalloc(n_u: int, n_v: int, off_u, adj_u, off_v, adj_v, q: int, stream=None) -> int:
@@ -418,6 +432,19 @@ def count_p2_noalloc(n_u: int, n_v: int, off_u, adj_u, off_v, adj_v, q: int, str
                                                ctypes.c_void_p(handle or 0), ctypes.byref(out)),
            "gbc_count_p2_noalloc")
     return out.value()
+
+
+def border_order(n_a: int, n_o: int, off_a, adj_a, iterations: int = 10_000, max_cand: int = 64):
+    """Border (Sec. V-B, Alg. 2) on the A -> O CSR (host arrays): the new id of
+    every O vertex, and the 1-blocks before (degree order) and after."""
+    off, p_off = _ptr_host(off_a)
+    adj, p_adj = _ptr_host(adj_a if len(adj_a) else np.zeros(1, np.int32))
+    out = np.zeros(max(1, n_o), dtype=np.int32)
+    before, after = _i64(), _i64()
+    _check(load_library().gbc_border_order(n_a, n_o, ctypes.c_void_p(p_off), ctypes.c_void_p(p_adj), iterations,
+                                           max_cand, ctypes.c_void_p(out.ctypes.data), ctypes.byref(before),
+                                           ctypes.byref(after)), "gbc_border_order")
+    return out[:n_o], int(before.value), int(after.value)
 
 
 def measure_int_peaks(device: int = 0) -> dict:

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbc.so")
-SOURCES = ["gbc_prep.cu", "gbc_search.cu", "gbc_api.cu", "gbc_noalloc.cu", "gbc_peaks.cu", "gbc_list.cu", "gbc_csr.cu"]
+SOURCES = ["gbc_prep.cu", "gbc_search.cu", "gbc_api.cu", "gbc_noalloc.cu", "gbc_peaks.cu", "gbc_list.cu", "gbc_csr.cu", "gbc_border.cu"]
 HEADERS = ["gbc_internal.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

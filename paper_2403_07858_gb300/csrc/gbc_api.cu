@@ -323,7 +323,7 @@ static void renumber_by_degree(int32_t nU, int32_t nV, const int32_t *offU, cons
 
 static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU,
                               const int32_t *adjU, const int32_t *offV, const int32_t *adjV, bool host,
-                              gbc_graph_t *out) {
+                              gbc_graph_t *out, int32_t flags = 0) {
     if (!ctx || !out || !offU || !offV) return fail(GBC_ERR_ARG, "gbc_load_graph: null argument");
     if (nU < 0 || nV < 0) return fail(GBC_ERR_ARG, "gbc_load_graph: negative vertex count");
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -410,7 +410,17 @@ static gbc_status load_common(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32
         return cleanup(fail(GBC_ERR_INVALID_GRAPH, "gbc_load_graph: %s", why));
     }
     // renumber both sides by degree (on the host) and replace the device copies
-    {
+    if (flags & GBC_LOAD_KEEP_IDS) {
+        g->callerU_h.resize((size_t)nU);
+        g->callerV_h.resize((size_t)nV);
+        for (int32_t u = 0; u < nU; ++u) g->callerU_h[u] = u;
+        for (int32_t v = 0; v < nV; ++v) g->callerV_h[v] = v;
+        CKG(cudaMallocAsync((void **)&g->callerU, std::max<size_t>(nU, 1) * 4, st));
+        CKG(cudaMallocAsync((void **)&g->callerV, std::max<size_t>(nV, 1) * 4, st));
+        if (nU) CKG(cudaMemcpyAsync(g->callerU, g->callerU_h.data(), (size_t)nU * 4, cudaMemcpyHostToDevice, st));
+        if (nV) CKG(cudaMemcpyAsync(g->callerV, g->callerV_h.data(), (size_t)nV * 4, cudaMemcpyHostToDevice, st));
+        CKG(cudaStreamSynchronize(st));
+    } else {
         std::vector<int32_t> hoffU, hadjU, hoffV, hadjV;
         const int32_t *pOffU = offU, *pAdjU = adjU, *pOffV = offV;
         if (!host) {
@@ -501,6 +511,13 @@ extern "C" gbc_status gbc_load_graph(gbc_ctx_t ctx, int32_t nU, int32_t nV, cons
                                      const int32_t *adjU, const int32_t *offV, const int32_t *adjV,
                                      gbc_graph_t *out) {
     return load_common(ctx, nU, nV, offU, adjU, offV, adjV, true, out);
+}
+
+extern "C" gbc_status gbc_load_graph_ex(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU,
+                                        const int32_t *adjU, const int32_t *offV, const int32_t *adjV,
+                                        int32_t flags, gbc_graph_t *out) {
+    if (flags & ~GBC_LOAD_KEEP_IDS) return fail(GBC_ERR_ARG, "gbc_load_graph_ex: unknown flags 0x%x", flags);
+    return load_common(ctx, nU, nV, offU, adjU, offV, adjV, true, out, flags);
 }
 
 extern "C" gbc_status gbc_load_graph_device(gbc_ctx_t ctx, int32_t nU, int32_t nV, const int32_t *offU_d,
@@ -756,6 +773,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         a.lib_begin = 0;
         a.lib_end = a.g.nA;
         a.cand_base = 0;
+        a.position_order = opt ? opt->position_order : 0;
         if (opt && opt->root_end > opt->root_begin) {
             a.root_begin = std::max(0, opt->root_begin);
             a.root_end = std::min(a.g.nA, opt->root_end);

@@ -183,6 +183,7 @@ struct CountArgs {
     // cand_root point so that the piece's global offsets land in its buffers.
     int32_t lib_begin, lib_end;
     int64_t cand_base;
+    int32_t position_order;  // 0: a root's positions most shared first; 1: in N(u)'s (id) order
     // root classification
     int32_t *omega;          // [nA] oriented wedge count of each root
     int32_t *tier_list;      // 3 lists of roots, each of capacity nA

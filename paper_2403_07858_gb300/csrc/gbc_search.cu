@@ -323,7 +323,9 @@ __device__ void process_root(const CountArgs &a, int32_t u, int32_t *keys, int32
         const int32_t cnt = __ldcg(&pc[i]);
         if (cnt > 0) {
             const int t = atomicAdd(&shared_int[1], 1);
-            sortbuf[t] = ((uint64_t)(0xffffffffu - (uint32_t)cnt) << 32) | (uint32_t)i;
+            // most shared first; or, on request, the other side's id order (N(u)'s order)
+            sortbuf[t] = a.position_order ? (uint64_t)(uint32_t)i
+                                          : ((uint64_t)(0xffffffffu - (uint32_t)cnt) << 32) | (uint32_t)i;
         }
     }
     G::sync();
