@@ -635,7 +635,8 @@ def serve_workload(args, rank, world, local):
     torch.cuda.set_device(local)
     gbc.build()
     t0 = time.perf_counter()
-    graphs = [bipgen.serving_graph(i, args.serve_scale) for i in range(8)]
+    with mp.get_context("spawn").Pool(8) as pool:
+        graphs = pool.starmap(bipgen.serving_graph, [(i, args.serve_scale) for i in range(8)])
     t_gen = time.perf_counter() - t0
     ctx = gbc.Context(local)
     hs = [ctx.load(g) for g in graphs]
@@ -657,7 +658,8 @@ def serve_workload(args, rank, world, local):
     for ri, f in enumerate([0.25, 0.5, 1.0, 2.0, 4.0]):
         lam = f * mu
         qs = stream[:24] + stream[24 + ri * args.serve_per_rate: 24 + (ri + 1) * args.serve_per_rate]
-        qs = qs[:max(24, min(len(qs), int(lam * 120) + 24))]
+        # about a minute of arrivals per rate, at least 8 queries
+        qs = qs[:int(min(len(qs), max(8, lam * 60)))]
         arrivals = np.cumsum(rng.exponential(1.0 / lam, len(qs)))
         done_at, status = [None] * len(qs), [None] * len(qs)
         pool = cf.ThreadPoolExecutor(max_workers=64)
@@ -671,7 +673,7 @@ def serve_workload(args, rank, world, local):
             except gbc.CountTimeout:
                 status[i] = "timeout"
             except gbc.GbcError as e:
-                status[i] = f"error {e.status}"
+                status[i] = f"error {e.status}: {str(e)[:120]}"
             done_at[i] = time.perf_counter() - start
 
         for i, (gi, p, q) in enumerate(qs):
@@ -685,7 +687,7 @@ def serve_workload(args, rank, world, local):
         lat = [done_at[i] - arrivals[i] for i in range(len(qs))]
         answered = [i for i in range(len(qs)) if isinstance(status[i], int)]
         lat_ok = [lat[i] for i in answered] or [float("nan")]
-        for i, key in enumerate(qs[:24]):
+        for i, key in enumerate(qs[:min(24, len(qs))]):
             # a query that finished alone may pass its deadline in a crowded mix:
             # only two finished counts can disagree
             if isinstance(alone[key], int) and isinstance(status[i], int) and status[i] != alone[key]:
@@ -697,7 +699,8 @@ def serve_workload(args, rank, world, local):
                       "p99_ms": 1e3 * float(np.percentile(lat_ok, 99)),
                       "p99_all_ms": 1e3 * float(np.percentile(lat, 99)),
                       "timeouts": sum(1 for x in status if x == "timeout"),
-                      "errors": sum(1 for x in status if isinstance(x, str) and x != "timeout")})
+                      "errors": sum(1 for x in status if isinstance(x, str) and x != "timeout"),
+                      "error_kinds": sorted({x for x in status if isinstance(x, str) and x != "timeout"})})
     stats = ctx.serve_stats()
     ctx.serve_stop()
     best = max(r["served_qps"] for r in rates)

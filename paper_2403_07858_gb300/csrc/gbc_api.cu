@@ -840,8 +840,18 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             while (slots < 2 * (int64_t)h.omega_max[2]) slots <<= 1;
             while (sortcap < h.omega_max[2]) sortcap <<= 1;
             a.slab_words = 2 * slots + 2 * sortcap;
-            const int grid2 = std::min(ctx->n_sms * 2, h.tier_count[2]);
-            CK(sc.get(&a.slab, (size_t)a.slab_words * grid2));
+            // one slab per CTA of the global-table tier, as many CTAs as fit in a
+            // quarter of the context's budget (at least one): a root's table must
+            // fit whole (the exact footprints that serving reserves include them)
+            const size_t slab_bytes = (size_t)a.slab_words * 4;
+            const int64_t fit = (int64_t)(ctx->budget / 4 / slab_bytes);
+            if (fit < 1) {
+                J.set_error(GBC_ERR_OOM, "gbc_count: a root's wedge table (%zu B) exceeds a quarter of the budget",
+                            slab_bytes);
+                continue;
+            }
+            a.slab_ctas = (int32_t)std::min<int64_t>(std::min(ctx->n_sms * 2, h.tier_count[2]), fit);
+            CK(sc.get(&a.slab, (size_t)a.slab_words * a.slab_ctas));
         }
         if (a.k >= 3 || J.list_mode) {
             const int64_t nA = a.g.nA;
@@ -1744,12 +1754,16 @@ extern "C" gbc_status gbc_serve_start(gbc_ctx_t ctx, int workers, int max_batch,
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->server) return fail(GBC_ERR_ARG, "gbc_serve_start: already serving");
     CK(cudaSetDevice(ctx->device));
+    // the context's budget, but no more than the device memory free now (the
+    // resident graphs were loaded after the budget was set)
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
     Server *sv = new Server();
     const int nw = workers ? workers : 4;
     sv->max_batch = max_batch ? max_batch : 256;
     sv->max_queue = max_queue ? max_queue : 4096;
     sv->time_limit_ms = time_limit_ms;
-    sv->budget = ctx->budget;
+    sv->budget = std::min(ctx->budget, (size_t)(0.9 * (double)free_b));
     sv->lanes.resize(nw);
     for (int w = 0; w < nw; ++w) {
         cudaStream_t s = nullptr;

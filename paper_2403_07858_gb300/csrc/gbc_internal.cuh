@@ -211,6 +211,7 @@ struct CountArgs {
     // global-tier hash slabs
     int32_t *slab;           // per-CTA slabs for roots with large omega
     int64_t slab_words;      // int32 words per CTA slab
+    int32_t slab_ctas;       // CTAs (and slabs) of the global-table tier
     // results
     unsigned long long *acc;        // [2] (lo, hi)
     unsigned long long *per_root;   // [2*nA] or null

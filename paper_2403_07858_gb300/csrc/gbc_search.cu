@@ -456,7 +456,7 @@ cudaError_t launch_candidates(const CountArgs &a, bool build, const int32_t *tie
         ++t_launches;
     }
     if (tier_counts_host[2] > 0) {
-        int grid = std::min(n_sms * 2, tier_counts_host[2]);
+        const int grid = a.slab_ctas;  // one global table slab per CTA
         if (build) k_cand_cta<true, true><<<grid, kCtaThreads, 0, st>>>(a);
         else k_cand_cta<false, true><<<grid, kCtaThreads, 0, st>>>(a);
         ++t_launches;
