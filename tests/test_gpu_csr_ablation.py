@@ -45,3 +45,14 @@ def test_csr_on_complete_graphs(gpu_ctx, m, n, p, q):
     h = gpu_ctx.load(bipgen.complete(m, n))
     assert h.count_ex(p, q, kernel="csr")[0] == math.comb(m, p) * math.comb(n, q)
     h.close()
+
+
+def test_csr_stops_at_its_deadline(gpu_ctx):
+    import time
+    import paper_2403_07858_gb300 as gbc
+    h = gpu_ctx.load(bipgen.complete(128, 128))  # (8,8): C(128,8)^2 ~ 2e24 bicliques, far beyond the limit
+    t0 = time.perf_counter()
+    with pytest.raises(gbc.CountTimeout):
+        h.count_ex(8, 8, kernel="csr", time_limit_ms=300)
+    assert time.perf_counter() - t0 < 10.0
+    h.close()

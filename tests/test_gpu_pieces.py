@@ -67,3 +67,28 @@ def test_a_root_larger_than_the_budget_is_reported():
         h.close()
     finally:
         ctx.close()
+
+
+def test_pieces_inside_a_batch():
+    import paper_2403_07858_gb300 as gbc
+    gbc.build()
+    g = bipgen.workload_small()
+    rec = json.load(open(GOLDEN))
+    pairs = [(3, 3), (4, 4), (5, 5), (2, 3)]
+    roomy = gbc.Context(0)
+    try:
+        h = roomy.load(g)
+        alone = [h.count_ex(p, q)[1]["scratch_bytes"] for p, q in pairs]
+        h.close()
+    finally:
+        roomy.close()
+    # half of what the jobs hold when they all run at once (plus one set of the
+    # |E|-sized position maps): the batch must split into waves or pieces
+    tight = gbc.Context(0, mem_budget_bytes=sum(alone) // 2 + 8 * g.n_edges)
+    try:
+        h = tight.load(g)
+        got = tight.count_batch([h] * len(pairs), [p for p, _ in pairs], [q for _, q in pairs])
+        assert got == [int(rec["counts"][f"{p},{q}"]) for p, q in pairs]
+        h.close()
+    finally:
+        tight.close()
