@@ -276,6 +276,7 @@ def main():
         for k in pqs:
             assert h.count(k, k) == ref_counts[k]
     step_ms, enum_ms, enum_words, enum_launches, launches = [], 0.0, 0, 0, 0
+    tail = {}  # per p = q: the enumeration launch's longest unit and its warps' exit spread
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush outside the timed region
@@ -292,11 +293,14 @@ def main():
             torch.cuda.synchronize()
             barrier()
             step_ms.append(e0.elapsed_time(e1))
-            for info in infos:
+            for k, info in zip(pqs, infos):
                 launches += info["launches"]
                 if info["set_size"] >= 4 and info["ms_enumerate"] > 0:
                     enum_ms += info["ms_enumerate"]
                     enum_launches += 1
+                    tail[str(k)] = {"launch_ms": info["enum_span_ms"],
+                                    "longest_unit_ms": info["enum_longest_unit_ms"],
+                                    "warp_exit_spread_ms": info["enum_exit_spread_ms"]}
     clocks = clk.summary()
     # Algorithmic work of the enumeration launches (untimed): the model words
     # of the search nodes the enumeration kernel evaluates, counted by the
@@ -372,7 +376,7 @@ def main():
                 "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
                 "model_words_per_launch": words_per_launch,
                 "loaded_words_per_launch": enum_words / len(model_words),
-                "launches": enum_launches, "ms_per_launch": ms_per_launch,
+                "launches": enum_launches, "ms_per_launch": ms_per_launch, "tail": tail,
                 "int32_lanes_peak_tops": n_sms * 128 * sm_max * 1e6 / 1e12,
                 "microbench": {
                     "and_popc_add_loop_words_per_s": micro["and_popc_words_per_s"],

@@ -178,6 +178,11 @@ typedef struct {
                                    the context's budget and it ran in independent pieces (Sec. VI) */
     int64_t words_enum;         /* the part of words_r + words_l that belongs to the nodes the
                                    enumeration kernel evaluates (|L| >= 3; stats) */
+    float enum_span_ms;         /* the enumeration launch, first warp start to last warp exit */
+    float enum_longest_unit_ms; /* its longest level-2 unit */
+    float enum_exit_spread_ms;  /* how long before the launch's end its warps left, on average
+                                   (the launch's tail) */
+    int32_t reserved_t;
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */

@@ -73,7 +73,9 @@ class CountInfo(ctypes.Structure):
                 ("ms_candidates", ctypes.c_float), ("ms_pairs", ctypes.c_float),
                 ("ms_enumerate", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("pieces", ctypes.c_int32),
-                ("words_enum", ctypes.c_int64)]
+                ("words_enum", ctypes.c_int64), ("enum_span_ms", ctypes.c_float),
+                ("enum_longest_unit_ms", ctypes.c_float), ("enum_exit_spread_ms", ctypes.c_float),
+                ("reserved_t", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {
@@ -95,6 +97,9 @@ class CountInfo(ctypes.Structure):
             "words_enum": int(self.words_enum),
             "launches": int(self.launches),
             "pieces": int(self.pieces),
+            "enum_span_ms": float(self.enum_span_ms),
+            "enum_longest_unit_ms": float(self.enum_longest_unit_ms),
+            "enum_exit_spread_ms": float(self.enum_exit_spread_ms),
         }
 
 

@@ -580,6 +580,7 @@ struct Small {
     unsigned long long deadline;
     unsigned long long enum_words;
     int32_t fin[2];   // completion counters (DoneRec publishing)
+    unsigned long long tail[5];  // enumeration launch: start, last exit, exit sum (us), longest unit, warps
 };
 
 // One count of a (possibly one-element) batch.
@@ -790,6 +791,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         a.cand_max = &s->cand_max;
         a.deadline = &s->deadline;
         a.enum_words = &s->enum_words;
+        a.tail = s->tail;
         a.stats = d_stats;
         a.per_root = J.per_root;
         J.trivial = (a.k > a.g.nA) || (a.kq > a.g.maxdegA) || a.g.nA == 0;
@@ -1319,6 +1321,18 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         inf.enum_words = (int64_t)J.h.enum_words;
         inf.launches = t_launches;
         inf.pieces = J.pieces;
+        {
+            // the enumeration launch's longest unit and how long before its end its
+            // warps left on average (every warp of the launch times its own exit)
+            const unsigned long long *tl = J.h.tail;
+            inf.enum_longest_unit_ms = (float)((double)tl[3] / 1e6);
+            if (tl[0] && tl[1] > tl[0] && tl[4] > 0) {
+                const double span_ms = ((double)tl[1] - (double)tl[0]) / 1e6;
+                const double mean_exit_ms = (double)tl[2] / 1e3 / (double)tl[4];
+                inf.enum_span_ms = (float)span_ms;
+                inf.enum_exit_spread_ms = (float)(span_ms - mean_exit_ms);
+            }
+        }
         *info = inf;
     }
     if (out) {

@@ -219,6 +219,9 @@ struct CountArgs {
     SearchStats *stats;             // or null
     unsigned long long *deadline;   // [1] globaltimer (ns) past which kernels stop; 0 = none
     unsigned long long *enum_words; // [1] C_R + C_L words read by the enumeration kernel
+    unsigned long long *tail;       // [5] enumeration launch (globaltimer): start (ns), last warp
+                                    // exit (ns), sum of warp exits after the start (us), longest
+                                    // unit (ns), warps
     int32_t *poscnt;                // [|E|] per anchor edge slot: candidates containing that position
     int32_t *posmap;                // [|E|] per anchor edge slot: its bit position in the R rows
     DoneRec *done;                  // host-mapped completion record, or null (no early release)

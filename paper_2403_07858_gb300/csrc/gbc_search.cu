@@ -848,6 +848,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     bool ovf = false;
     unsigned long long st_evals[2] = {0, 0}, st_passed[2] = {0, 0}, st_wr = 0, st_wl = 0;
     const int total_units = *n_units;
+    // the launch's start: the first warp to get here sets it
+    if (lane == 0) atomicCAS(a0.tail, 0ull, global_ns());
+    // each unit's start time, kept in the warp's shared scalars (no register)
+    unsigned long long *t_unit = reinterpret_cast<unsigned long long *>(spanp + kMaxPQ);
     while (true) {
         int guidx = 0;
         if (lane == 0) guidx = atomicAdd(queue, 1);
@@ -888,6 +892,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         // word wi of R row x (rows are stored word-major in pairs)
         auto r_word = [&](int32_t x, uint32_t wi) { return Rw[2 * ((int64_t)(wi >> 1) * c + x) + (wi & 1u)]; };
         u128 unit_acc = 0;
+        if (lane == 0) *t_unit = global_ns();
         // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
         {
             for (int pw = lane; pw < npairs; pw += 32) CR(0)[pw] = Rp[pw * c + j];
@@ -1190,7 +1195,16 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (STATS) atomicAdd(a.enum_words, words);
         }
         unit_done();
+        if (lane == 0) atomicMax(a0.tail + 3, global_ns() - *t_unit);  // longest unit of the launch
         ovf = false;
+    }
+    if (lane == 0) {
+        // this warp's exit: how long after the launch's start the warps leave
+        const unsigned long long te = global_ns();
+        const unsigned long long t0 = *(volatile unsigned long long *)a0.tail;
+        atomicMax(a0.tail + 1, te);
+        atomicAdd(a0.tail + 2, te > t0 ? (te - t0) / 1000ull : 0ull);
+        atomicAdd(a0.tail + 4, 1ull);
     }
     if (STATS) {
         const CountArgs &a = a0;  // statistics are kept for single-job launches
