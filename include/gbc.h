@@ -133,7 +133,8 @@ gbc_status gbc_count(gbc_graph_t g, int p, int q, gbc_u128 *out);
 /* Options of gbc_count_ex; zero-initialise for the defaults. */
 typedef struct {
     int32_t anchor;      /* gbc_anchor; GBC_ANCHOR_AUTO = cost model picks */
-    int32_t collect_stats; /* 1: fill gbc_count_info's search-tree counters (slower) */
+    int32_t collect_stats; /* 1: fill gbc_count_info's search-tree counters (slower); 2: fill
+                              words_exec and collapsed instead (the executed traversal) */
     int32_t enum_warps;  /* warps of the persistent enumeration launch; 0 = auto */
     int32_t time_limit_ms; /* > 0: device-side deadline; past it the kernels stop and the
                               call returns GBC_ERR_TIMEOUT (the count is then not valid) */
@@ -150,6 +151,13 @@ typedef struct {
                                0 = most shared position first (the default), 1 = the other side's
                                id order (on a graph relabelled by gbc_border_order: Border's order,
                                Sec. V-B); the count does not depend on it */
+    int32_t no_collapse;  /* 1: enter every node of the bitmap enumeration.  0 (the default): a node
+                             whose C_R holds at most q' + 2 positions (q' the set size on the other
+                             side) adds its whole subtree in closed form instead, sum over the
+                             q'-subsets Q of C_R of C(|C_L with every vertex of Q|, vertices still
+                             to add) -- the subtree's leaves counted from the other side (Def. 1);
+                             the count does not depend on it.  collect_stats = 1 always enters
+                             every node. */
 } gbc_count_options;
 
 /* Set representation of the enumeration (gbc_count_options.kernel). */
@@ -183,6 +191,11 @@ typedef struct {
     float enum_exit_spread_ms;  /* how long before the launch's end its warps left, on average
                                    (the launch's tail) */
     int32_t reserved_t;
+    int64_t words_exec;         /* words of the traversal the enumeration kernel executes: the
+                                   C_R / C_L words of every node it evaluates (as in words_enum),
+                                   plus, per collapsed subtree, its C_L words and |C_R| T words per
+                                   nonzero C_L word (collect_stats = 2) */
+    int64_t collapsed;          /* subtrees the enumeration counted in closed form (collect_stats = 2) */
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */

@@ -693,6 +693,9 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                            const DoneFn *on_done = nullptr) {
     cudaStream_t st = lane.st;
     const int n = (int)jobs.size();
+    // statistics of the full traversal (1) or of the executed one (2); subtree collapse unless turned off
+    const int enum_mode = want_stats ? (opt && opt->collect_stats == 2 ? 2 : 1) : 0;
+    const bool collapse = !(opt && opt->no_collapse);
     Scratch sc(st);
     Small *d_small = nullptr;
     CK(sc.get(&d_small, n));
@@ -1027,7 +1030,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                 CK(cudaMemsetAsync(d_queue, 0, 4, st));
                 CK(cudaMemcpyAsync(d_job, &b, sizeof(CountArgs), cudaMemcpyHostToDevice, st));
                 CK(launch_sort_units(u_all, u_bucket, ucnt, ucnt + 1, ucnt + 17, u_sorted, nc, st));
-                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, want_stats, warps_for(std::vector<int>{i}),
+                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, enum_mode, collapse, warps_for(std::vector<int>{i}),
                                     (int)row_stride(a.g.maxdegA), (std::max(hs[i].cand_max, 1) + 31) / 32, a.k,
                                     ctx->n_sms, st));
             }
@@ -1225,7 +1228,7 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                                cudaMemcpyHostToDevice, st));
             CK(launch_sort_units(units_all, units_bucket, ucounters, ucounters + 1, ucounters + 17, units_sorted,
                                  unit_cap, st));
-            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, want_stats, warps_for(wave),
+            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, enum_mode, collapse, warps_for(wave),
                                 max_wr, max_wl, max_k, ctx->n_sms, st));
             // the job table is read by the launch: keep the host copy alive until it has run
             if (on_done) CK(wait_releasing(wave));
@@ -1309,6 +1312,8 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         inf.words_r = (int64_t)hs.words_r;
         inf.words_l = (int64_t)hs.words_l;
         inf.words_enum = (int64_t)hs.words_enum;
+        inf.words_exec = (int64_t)hs.words_exec;
+        inf.collapsed = (int64_t)hs.collapsed;
         inf.scratch_bytes = (int64_t)J.scratch_bytes;
         if (!J.trivial && J.a.k >= 2) {
             inf.ms_candidates = tm.between(0, 1);

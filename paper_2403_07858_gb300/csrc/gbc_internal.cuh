@@ -150,6 +150,9 @@ struct SearchStats {
     unsigned long long words_r;
     unsigned long long words_l;
     unsigned long long words_enum;  // the part of words_r + words_l of nodes k_enumerate evaluates
+    unsigned long long words_exec;  // words of the traversal k_enumerate executes (collapsed subtrees
+                                    // as their C_L and T words)
+    unsigned long long collapsed;   // subtrees k_enumerate counted in closed form
 };
 
 // Sets the text gbc_last_error() returns on the calling thread.
@@ -337,8 +340,11 @@ cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, cons
 // One persistent launch over the sorted level-2 units of several counts
 // (d_jobs: a device array of their CountArgs, indexed by the units' job id).
 // d_queue: a zeroed int32 work counter.
+// mode: 0 the count, 1 with the full traversal's statistics, 2 with the words of
+// the executed traversal.  collapse: count subtrees of nodes with |C_R| <= kq + 2
+// in closed form (never in mode 1).
 cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
-                             bool stats, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             int mode, bool collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
                              cudaStream_t st);
 
 }  // namespace gbc

@@ -748,6 +748,7 @@ constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word
 struct EnumLayout {
     int wr, wl;     // row capacities in words (both even)
     int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
+    int collapse;   // 1: count the subtree of a node with |C_R| <= kq + 2 in closed form
     // per warp: parents (kParents x uint4) | their word indices (kParents) | leaf masks | leaf tags |
     // levels x (CR | CL | xs) | scalars
     __host__ __device__ int staging_words() const { return kParents * 5 + 2 * kLeafList; }
@@ -809,10 +810,23 @@ __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c
 
 constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never above 2^128)
 
-template <bool STATS>
+// Which subtrees collapse: C_R minus a skip set of s = m - kq positions is one
+// kq-subset per lane, so C(m, s) <= 32; s <= 2 keeps the per-word work small.
+__device__ __forceinline__ bool collapsible(int m, int kq) {
+    const int s = m - kq;
+    return s == 0 || (s == 1 && m <= 32) || (s == 2 && m * (m - 1) <= 64);
+}
+
+// MODE 0: the count.  MODE 1: the count with the search-tree statistics of the
+// full traversal (every node evaluated, no collapse), which equal the oracle's.
+// MODE 2: the count with the words of the traversal this kernel executes
+// (collapsed subtrees included), for the roofline.
+template <int MODE>
 __global__ void __launch_bounds__(256, 4)
 k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, int32_t *queue, EnumLayout lay,
             uint32_t *gstack) {
+    constexpr bool STATS = MODE == 1;
+    constexpr bool WORK = MODE == 2;
     extern __shared__ __align__(16) uint32_t smem_stack[];
     __shared__ ulonglong2 s_binom[kSmemBinom];
     const int lane = threadIdx.x & 31;
@@ -847,6 +861,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
 
     bool ovf = false;
     unsigned long long st_evals[2] = {0, 0}, st_passed[2] = {0, 0}, st_wr = 0, st_wl = 0;
+    unsigned long long wk_words = 0, wk_nodes = 0;  // executed words and collapsed nodes (WORK)
     const int total_units = *n_units;
     // the launch's start: the first warp to get here sets it
     if (lane == 0) atomicCAS(a0.tail, 0ull, global_ns());
@@ -893,13 +908,77 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         auto r_word = [&](int32_t x, uint32_t wi) { return Rw[2 * ((int64_t)(wi >> 1) * c + x) + (wi & 1u)]; };
         u128 unit_acc = 0;
         if (lane == 0) *t_unit = global_ns();
+        // Collapse of a node's subtree (C_R = cr over nsp pairs holding m
+        // positions, C_L = cl from word lo, jrem vertices still to add).  The
+        // subtree adds C(|C_R & R_Z|, kq) for every jrem-subset Z of C_L (its
+        // pruning only skips zero terms), and summing over the kq-subsets Q of
+        // C_R instead gives  sum_Q C(n_Q, jrem),  n_Q = |C_L & T_Q|  where T_Q
+        // is the AND of the T rows (candidates containing a position) of Q:
+        // the same (L, R) pairs counted from the other side (Def. 1).  Lane t
+        // takes the t-th Q, i.e. C_R without its skip set of m - kq positions.
+        auto collapse = [&](const uint2 *cr, int nsp, int m, const uint32_t *cl, int lo, int jrem, int32_t *posbuf) {
+            int cur = 0;
+            gather_children(reinterpret_cast<const uint32_t *>(cr), 2 * nsp, 64 * nsp, cur, posbuf);
+            const int s = m - kq;
+            const int pos = lane < m ? posbuf[lane] : 0;
+            const int nsub = s == 0 ? 1 : (s == 1 ? m : m * (m - 1) / 2);
+            uint32_t skip = 0;
+            if (s == 1 && lane < nsub) {
+                skip = 1u << lane;
+            } else if (s == 2 && lane < nsub) {
+                int t = lane, i0 = 0;  // the lane-th pair i0 < i1 < m
+                while (i0 < m - 2 && t >= m - 1 - i0) { t -= m - 1 - i0; ++i0; }
+                skip = (1u << i0) | (1u << (i0 + 1 + t));
+            }
+            int n = 0, nzw = 0;
+            for (int w0 = lo; w0 < WL; w0 += 32) {
+                const uint32_t cwl = w0 + lane < WL ? cl[w0 + lane] : 0u;
+                uint32_t nz = __ballot_sync(kFull, cwl != 0u);
+                if (WORK) nzw += __popc(nz);
+                while (nz) {
+                    const int b = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const uint32_t cw = __shfl_sync(kFull, cwl, b);
+                    const uint32_t tv = lane < m ? Tb[(int64_t)(w0 + b) * P + pos] : ~0u;
+                    if (s == 0) {
+                        n += __popc(cw & __reduce_and_sync(kFull, tv));
+                    } else {
+                        uint32_t acc = cw;
+                        for (int l = 0; l < m; ++l) {
+                            const uint32_t v = __shfl_sync(kFull, tv, l);
+                            if (!((skip >> l) & 1u)) acc &= v;
+                        }
+                        n += __popc(acc);
+                    }
+                }
+            }
+            if (lane < nsub && n >= jrem) {
+                if (jrem == kq && smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                else add_u128(unit_acc, binom_lookup(a.binom, jrem, n, ovf), ovf);
+            }
+            if (WORK && lane == 0) { wk_words += (unsigned long long)(WL - lo) + (unsigned long long)m * nzw; wk_nodes += 1; }
+            __syncwarp();
+        };
+        const bool may_collapse = !STATS && lay.collapse && k >= 4;
         // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
+        bool unit_collapsed = false;
         {
-            for (int pw = lane; pw < npairs; pw += 32) CR(0)[pw] = Rp[pw * c + j];
+            int mc = 0;
+            for (int pw = lane; pw < npairs; pw += 32) {
+                const uint2 v = Rp[pw * c + j];
+                CR(0)[pw] = v;
+                mc += __popc(v.x) + __popc(v.y);
+            }
             const int lo = (j + 1) >> 5;
             for (int w = lo + lane; w < WL; w += 32) CL(0)[w] = St[(int64_t)w * c + j];
             const int sp = row_span_pairs(Rp, c, j, npairs);
             if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; spanp[0] = sp; }
+            mc = __reduce_add_sync(kFull, mc);
+            __syncwarp();
+            if (may_collapse && collapsible(mc, kq)) {
+                collapse(CR(0), sp, mc, CL(0), lo, k - 2, XS(0));
+                unit_collapsed = true;
+            }
         }
         __syncwarp();
         int nl = 0, npar = 0;  // staged leaf words and their parents (warp-uniform)
@@ -921,6 +1000,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     const uint32_t *Tw = Tb + (int64_t)w * P;       // word w of every T row
                     const int m = __popc(cy.x) + __popc(cy.y) + __popc(cy.z) + __popc(cy.w);
                     if (STATS) st_evals[1] += __popc(M), st_wr += (unsigned long long)__popc(M) * WRm;
+                    if (WORK) wk_words += (unsigned long long)__popc(M) * WRm;
                     if (m < 16) {
                         uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
 #pragma unroll
@@ -988,7 +1068,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         };
         int lv = 0;
         unsigned batches = 0;
-        while (true) {
+        while (!unit_collapsed) {
             if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
             const uint32_t dm = dmask[lv];
             if (dm != 0) {
@@ -1001,19 +1081,27 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 uint2 *cr2 = CR(lv + 1);
                 const uint32_t *cl = CL(lv);
                 uint32_t *cl2 = CL(lv + 1);
-                int nsp = 0;
+                int nsp = 0, mc = 0;
                 for (int b = 0; b < sp; b += 32) {
                     const int pw = b + lane;
                     uint2 v = make_uint2(0, 0);
                     if (pw < sp) {
                         v = and2(cr[pw], Rp[pw * c + x]);
                         cr2[pw] = v;
+                        mc += __popc(v.x) + __popc(v.y);
                     }
                     const unsigned m = __ballot_sync(kFull, (v.x | v.y) != 0u);
                     if (m) nsp = b + 32 - __clz(m);
                 }
                 const int lo = (x + 1) >> 5;
                 for (int w = lo + lane; w < WL; w += 32) cl2[w] = cl[w] & St[(int64_t)w * c + x];
+                if (may_collapse) mc = __reduce_add_sync(kFull, mc);
+                __syncwarp();
+                if (may_collapse && collapsible(mc, kq)) {
+                    // the child (|L| = lv + 3) is counted whole, not entered
+                    collapse(cr2, nsp, mc, cl2, lo, k - (lv + 3), XS(lv + 1));
+                    continue;
+                }
                 if (lane == 0) { cursor[lv + 1] = x + 1; dmask[lv + 1] = 0; spanp[lv + 1] = nsp; }
                 __syncwarp();
                 ++lv;
@@ -1084,13 +1172,17 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     if (STATS) words += 2 * sp;
                 }
                 const bool ps = py && narrow;  // staged for phase B
-                if (STATS) {
+                if (STATS || WORK) {
                     const unsigned pm = __ballot_sync(kFull, py);
                     if (lane == 0) {
-                        st_evals[0] += got;
-                        st_passed[0] += __popc(pm);
-                        st_wr += (unsigned long long)got * WRm;
-                        st_wl += (unsigned long long)__popc(pm) * WL;
+                        if (STATS) {
+                            st_evals[0] += got;
+                            st_passed[0] += __popc(pm);
+                            st_wr += (unsigned long long)got * WRm;
+                            st_wl += (unsigned long long)__popc(pm) * WL;
+                        } else {
+                            wk_words += (unsigned long long)got * WRm + (unsigned long long)__popc(pm) * WL;
+                        }
                     }
                 }
                 const int lo_y = (y + 1) >> 5;
@@ -1135,6 +1227,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                             for (int pw = 0; pw < sp; ++pw) n += popc2(and2(cr[pw], Rp[pw * c + y]), Rp[pw * c + x]);
                             if (STATS) words += 2 * sp;
                             if (STATS) { st_evals[1] += 1; st_wr += WRm; }
+                            if (WORK) wk_words += WRm;
                             if (n >= kq) {
                                 if (STATS) st_passed[1] += 1;
                                 if (smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
@@ -1168,6 +1261,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 desc = m >= k - (ell + 1);
             }
             const unsigned dmb = __ballot_sync(kFull, desc);
+            if (WORK) {
+                const unsigned pm = __ballot_sync(kFull, pass);
+                if (lane == 0) wk_words += (unsigned long long)got * WRm + (unsigned long long)__popc(pm) * WL;
+            }
             if (STATS) {
                 const unsigned pm = __ballot_sync(kFull, pass);
                 if (lane == 0) {
@@ -1205,6 +1302,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         atomicMax(a0.tail + 1, te);
         atomicAdd(a0.tail + 2, te > t0 ? (te - t0) / 1000ull : 0ull);
         atomicAdd(a0.tail + 4, 1ull);
+    }
+    if (WORK) {
+        atomicAdd(&a0.stats->words_exec, wk_words);
+        atomicAdd(&a0.stats->collapsed, wk_nodes);
     }
     if (STATS) {
         const CountArgs &a = a0;  // statistics are kept for single-job launches
@@ -1248,9 +1349,9 @@ cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, cons
 }
 
 cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
-                             bool stats, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             int mode, bool collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
                              cudaStream_t st) {
-    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3)};
+    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3), collapse ? 1 : 0};
     if (max_wl >= (1 << kTagShift)) return cudaErrorInvalidValue;  // staged-word tags hold the word index in 24 bits
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;
@@ -1261,7 +1362,7 @@ cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const i
     uint32_t *gstack = nullptr;
     cudaError_t err;
     if (use_smem) {
-        auto kern = stats ? k_enumerate<true> : k_enumerate<false>;
+        auto kern = mode == 1 ? k_enumerate<1> : (mode == 2 ? k_enumerate<2> : k_enumerate<0>);
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         int per_sm = 0;
@@ -1272,8 +1373,8 @@ cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const i
     } else {
         err = cudaMallocAsync(reinterpret_cast<void **>(&gstack), per_warp * warps_per_cta * grid, st);
         if (err != cudaSuccess) return err;
-        if (stats) k_enumerate<true><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, units, n_units, d_queue, lay, gstack);
-        else k_enumerate<false><<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, units, n_units, d_queue, lay, gstack);
+        auto kern = mode == 1 ? k_enumerate<1> : (mode == 2 ? k_enumerate<2> : k_enumerate<0>);
+        kern<<<grid, 32 * warps_per_cta, 0, st>>>(d_jobs, units, n_units, d_queue, lay, gstack);
         ++t_launches;
         err = cudaGetLastError();
         cudaFreeAsync(gstack, st);

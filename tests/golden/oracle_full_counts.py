@@ -17,10 +17,13 @@ time, with those times, which the benchmark's CPU baseline re-times on the
 GPU host to scale this machine's full-count time to that host.
 
 A count whose wall time passes --budget-s is recorded as "oracle unavailable
-at this size (budget X s)" instead.
+at this size (budget X s)" instead.  With --checkpoint, every finished chunk of
+roots is appended to a JSON-lines file, and a later run resumes from it (its
+wall time adds up the segments).
 
     python tests/golden/oracle_full_counts.py --workload powerlaw2m [--cores N]
     python tests/golden/oracle_full_counts.py --workload dense_core
+    python tests/golden/oracle_full_counts.py --workload powerlaw2m --only 6:6 --checkpoint ck.jsonl
 """
 from __future__ import annotations
 
@@ -111,7 +114,25 @@ def pps_sample(secs: np.ndarray, target_s: float, seed: int, cap_s: float) -> li
     return sorted({int(order[i]) for i in picks})
 
 
-def run_count(g, make, p, q, anchor, cores, budget_s, log):
+def _read_checkpoint(path, key):
+    """Finished chunks of one count from an append-only checkpoint (JSON lines),
+    and the wall time of every earlier segment of the run (its largest elapsed)."""
+    chunks, seg_wall = [], {}
+    if path and os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                try:
+                    rec = json.loads(line)
+                except ValueError:  # a line cut off when a segment ended
+                    continue
+                if rec.get("k") != key:
+                    continue
+                chunks.append(rec)
+                seg_wall[rec["seg"]] = max(seg_wall.get(rec["seg"], 0.0), rec["el"])
+    return chunks, sum(seg_wall.values())
+
+
+def run_count(g, make, p, q, anchor, cores, budget_s, log, checkpoint=None):
     n_a = g.n_u if anchor == "U" else g.n_v
     deg = np.diff(g.off_u if anchor == "U" else g.off_v)
     # heaviest (by degree) roots first, alone; the light tail in chunks
@@ -123,24 +144,44 @@ def run_count(g, make, p, q, anchor, cores, budget_s, log):
         i += size
     vals = [0] * n_a
     secs = np.zeros(n_a)
+    key = f"{p},{q},{anchor}"
+    earlier, earlier_wall = _read_checkpoint(checkpoint, key)
+    finished = np.zeros(n_a, dtype=bool)
+    for rec in earlier:
+        for r, x, t in zip(rec["roots"], rec["vals"], rec["secs"]):
+            vals[r] = int(x)
+            secs[r] = t
+            finished[r] = True
+    todo = [c for c in chunks if not all(finished[r] for r in c[3])]
+    done = int(finished.sum())
+    if earlier and log:
+        log(f"  ({p},{q}) anchor {anchor}: resuming with {done}/{n_a} roots from {checkpoint}, "
+            f"{earlier_wall:.0f} s of earlier wall time")
+    seg = f"{os.getpid()}-{time.time():.0f}"
+    ckf = open(checkpoint, "a") if checkpoint else None
     t0 = time.perf_counter()
-    done = 0
     over = False
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores, initializer=_init, initargs=(make,)) as pool:
-        for roots, v, s in pool.imap_unordered(_run_chunk, chunks):
+        for roots, v, s in pool.imap_unordered(_run_chunk, todo):
             for r, x, t in zip(roots, v, s):
                 vals[r] = x
                 secs[r] = t
             done += len(roots)
             el = time.perf_counter() - t0
-            if el > budget_s:
+            if ckf:
+                ckf.write(json.dumps({"k": key, "seg": seg, "el": round(el, 2), "roots": roots,
+                                      "vals": [str(x) for x in v], "secs": [round(t, 5) for t in s]}) + "\n")
+                ckf.flush()
+            if earlier_wall + el > budget_s:
                 over = True
                 pool.terminate()
                 break
             if log and done % 20000 < len(roots):
-                log(f"  ({p},{q}) anchor {anchor}: {done}/{n_a} roots, {el:.0f} s")
-    wall = time.perf_counter() - t0
+                log(f"  ({p},{q}) anchor {anchor}: {done}/{n_a} roots, {earlier_wall + el:.0f} s")
+    if ckf:
+        ckf.close()
+    wall = earlier_wall + time.perf_counter() - t0
     if over:
         return {"p": p, "q": q, "anchor": anchor,
                 "unavailable": f"oracle unavailable at this size (budget {budget_s:.0f} s on {cores} cores)"}
@@ -185,6 +226,8 @@ def main():
     ap.add_argument("--cores", type=int, default=len(os.sched_getaffinity(0)))
     ap.add_argument("--budget-s", type=float, default=4 * 3600.0, help="wall-time budget per count")
     ap.add_argument("--only", default="", help="comma-separated p,q pairs as p:q (default all)")
+    ap.add_argument("--checkpoint", default="",
+                    help="append every finished chunk to this JSON-lines file and resume from it")
     args = ap.parse_args()
     if args.trim_samples:
         rec = json.load(open(OUT))
@@ -210,7 +253,8 @@ def main():
         if only and (p, q) not in only:
             continue
         log(f"{args.workload} ({p},{q}) anchor {anchor} on {args.cores} cores")
-        res = run_count(g, w["make"], p, q, anchor, args.cores, args.budget_s, log)
+        res = run_count(g, w["make"], p, q, anchor, args.cores, args.budget_s, log,
+                        checkpoint=args.checkpoint or None)
         entry["counts"][f"{p},{q}"] = res
         rec[args.workload] = entry
         with open(OUT + ".tmp", "w") as f:
