@@ -306,13 +306,20 @@ def main():
     # of the search nodes the enumeration kernel evaluates, counted by the
     # statistics pass of the same counts (equal to the oracle's instrumented
     # traversal on the graphs the tests check).
-    model_words = {}
+    # The kernel collapses small-C_R subtrees, so the words it executes (the
+    # nodes it evaluates plus each collapsed subtree's C_L and T words) come
+    # from a second statistics pass with the collapse on.
+    model_words, exec_words, collapsed = {}, {}, 0
     for k in ([] if args.no_roofline else pqs):
         n, sinfo = h.count_ex(k, k, stats=True)
         assert n == ref_counts[k]
         if sinfo["words_enum"] > 0:
             model_words[k] = sinfo["words_enum"]
             enum_words += sinfo["enum_words"]
+            n, xinfo = h.count_ex(k, k, stats="exec")
+            assert n == ref_counts[k]
+            exec_words[k] = xinfo["words_exec"]
+            collapsed += xinfo["collapsed"]
     h.close()
     ms_step = statistics.mean(step_ms)
     if dist is not None:
@@ -351,20 +358,23 @@ def main():
 
     # ---- roofline of the dominant kernel (the enumeration).  ncu shows it bound
     # by instruction issue on the integer pipe with its bitmap rows resident in
-    # L1/L2, so the roofline is ALU.  Algorithmic work: per evaluated search node
-    # ceil(d/32) C_R words, plus ceil(c/32) C_L words for internal nodes, each
-    # word one AND and one POPC.  Peak: the POPC pipe, the narrower of the two,
+    # L1/L2, so the roofline is ALU.  Algorithmic work per launch: the words of
+    # the traversal the kernel executes -- per evaluated search node ceil(d/32)
+    # C_R words, plus ceil(c/32) C_L words for internal nodes; per collapsed
+    # subtree its C_L words and |C_R| T words per nonzero C_L word -- each word
+    # one AND and one POPC.  Peak: the POPC pipe, the narrower of the two,
     # retires 16 results per SM per clock (the register-only AND + POPC loop of
     # gbc_measure_int_peaks reaches that rate), so the SMs can do at most
-    # SMs x 16 x clock model words per second, two ops each.
+    # SMs x 16 x clock words per second, two ops each.
     peaks = _peaks()
     roof = None
-    if enum_launches and model_words:
+    if enum_launches and exec_words:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_words = n_sms * 16 * sm_max * 1e6
         peak_tops = 2.0 * peak_words / 1e12
-        words_per_launch = sum(model_words.values()) / len(model_words)
+        words_per_launch = sum(exec_words.values()) / len(exec_words)
+        model_per_launch = sum(model_words.values()) / len(model_words)
         ops_per_launch = 2.0 * words_per_launch
         ms_per_launch = enum_ms / enum_launches
         achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e12
@@ -372,17 +382,20 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                 "frac": achieved / peak_tops, "traffic": _ncu_traffic(), "kernel": "k_enumerate",
                 "peak_source": f"derived: {n_sms} SMs x 16 POPC/clk/SM x {sm_max:.0f} MHz max SM clock "
-                               "= model words/s, x 2 ops (AND + POPC) per word",
+                               "= words/s, x 2 ops (AND + POPC) per word",
                 "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
-                "model_words_per_launch": words_per_launch,
-                "loaded_words_per_launch": enum_words / len(model_words),
+                "executed_words_per_launch": words_per_launch,
+                "collapsed_subtrees_per_launch": collapsed / len(exec_words),
+                "full_traversal_model_words_per_launch": model_per_launch,
+                "full_traversal_model_words_per_s_over_peak": model_per_launch / (ms_per_launch * 1e-3) / peak_words,
+                "loaded_words_per_launch_full_traversal": enum_words / len(model_words),
                 "launches": enum_launches, "ms_per_launch": ms_per_launch, "tail": tail,
                 "int32_lanes_peak_tops": n_sms * 128 * sm_max * 1e6 / 1e12,
                 "microbench": {
                     "and_popc_add_loop_words_per_s": micro["and_popc_words_per_s"],
                     "loop_over_derived_peak": micro["and_popc_words_per_s"] / peak_words,
-                    "model_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
-                                                   / micro["and_popc_words_per_s"],
+                    "executed_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
+                                                      / micro["and_popc_words_per_s"],
                     "l2_and_popc_stream_gbs": micro["l2_bytes_per_s"] / 1e9}}
 
     # ---- the dense-core and the 256-graph batch workloads (extra keys of the line)
@@ -647,15 +660,20 @@ def serve_workload(args, rank, world, local):
     lim = args.serve_limit_ms
     stream = bipgen.serving_queries(24 + 5 * args.serve_per_rate, seed=600)
     # single stream: sequential plain counts of the first 24 queries
-    alone, serv_ms = {}, []
+    alone, serv_ms, single_answered = {}, [], 0
     for (gi, p, q) in stream[:24]:
         t = time.perf_counter()
         try:
             alone[(gi, p, q)] = hs[gi].count_ex(p, q, time_limit_ms=lim)[0]
+            single_answered += 1
         except gbc.CountTimeout:
             alone[(gi, p, q)] = "timeout"
         serv_ms.append((time.perf_counter() - t) * 1e3)
-    mu = 1e3 / statistics.mean(serv_ms)  # queries/s of one stream
+    # queries/s of one stream, every query (answered or past its deadline) taking
+    # its time: the base of the offered rates
+    mu = 1e3 / statistics.mean(serv_ms)
+    # answered queries/s of one stream: the figure the server's answered rate compares with
+    single_qps = single_answered / (sum(serv_ms) / 1e3)
     ctx.serve_start(workers=4, max_batch=64, max_queue=100_000, time_limit_ms=lim)
     rng = np.random.default_rng(601)
     rates, mismatches = [], 0
@@ -718,7 +736,14 @@ def serve_workload(args, rank, world, local):
                                       "queries: graph uniform, p,q uniform in {2..8}, Poisson arrivals",
                           "scale": args.serve_scale, "per_request_limit_ms": lim, "workers": 4,
                           "graph_generation_s": t_gen},
-               "single_stream_qps": mu, "rates": rates, "served_equals_alone_mismatches": mismatches,
+               "single_stream_qps": single_qps,
+               "single_stream": {"queries": 24, "answered": single_answered, "answered_qps": single_qps,
+                                 "service_rate_qps": mu,
+                                 "how": "the first 24 queries as sequential plain counts with the same deadline; "
+                                        "answered_qps counts answered queries only, service_rate_qps every "
+                                        "query (the base of the offered rates)"},
+               "served_over_single_stream": best / single_qps if single_qps > 0 else None,
+               "rates": rates, "served_equals_alone_mismatches": mismatches,
                "value_is": "answered queries/s (requests past their deadline are counted apart, as timeouts), "
                            "best over the rates; p50/p99 over answered requests, p99_all over all",
                "server": stats}

@@ -151,13 +151,14 @@ typedef struct {
                                0 = most shared position first (the default), 1 = the other side's
                                id order (on a graph relabelled by gbc_border_order: Border's order,
                                Sec. V-B); the count does not depend on it */
-    int32_t no_collapse;  /* 1: enter every node of the bitmap enumeration.  0 (the default): a node
-                             whose C_R holds at most q' + 2 positions (q' the set size on the other
-                             side) adds its whole subtree in closed form instead, sum over the
-                             q'-subsets Q of C_R of C(|C_L with every vertex of Q|, vertices still
-                             to add) -- the subtree's leaves counted from the other side (Def. 1);
-                             the count does not depend on it.  collect_stats = 1 always enters
-                             every node. */
+    int32_t collapse_skip; /* subtree collapse of the bitmap enumeration: a node whose C_R holds at
+                              most q' + s positions (q' the set size on the other side) adds its
+                              whole subtree in closed form instead of being entered: the sum over
+                              the q'-subsets Q of C_R of C(|C_L with every vertex of Q|, vertices
+                              still to add) -- the subtree's leaves counted from the other side
+                              (Def. 1).  0 = the default s (4); -1 = enter every node; 1..4 = that
+                              s (nodes needing more than 256 subsets Q are entered).  The count does
+                              not depend on it; collect_stats = 1 always enters every node. */
 } gbc_count_options;
 
 /* Set representation of the enumeration (gbc_count_options.kernel). */
@@ -196,6 +197,12 @@ typedef struct {
                                    plus, per collapsed subtree, its C_L words and |C_R| T words per
                                    nonzero C_L word (collect_stats = 2) */
     int64_t collapsed;          /* subtrees the enumeration counted in closed form (collect_stats = 2) */
+    int64_t enum_phase_cycles[10]; /* SM clock cycles the enumeration's warps spent per phase
+                                      (collect_stats = 2): 0 unit set-up, 1 collapsed subtrees,
+                                      2 child gathers, 3 internal-child tests, 4 descents, 5 nodes
+                                      whose children are leaf parents (gross: includes 7 and 8),
+                                      6 leaf counting at unit ends, 7 leaf counting inside 5,
+                                      8 lane-serial leaf walks inside 5, 9 unused */
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */

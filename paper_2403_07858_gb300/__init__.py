@@ -62,7 +62,7 @@ class CountOptions(ctypes.Structure):
                 ("enum_warps", ctypes.c_int32), ("time_limit_ms", ctypes.c_int32),
                 ("root_begin", ctypes.c_int32), ("root_end", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("position_order", ctypes.c_int32),
-                ("no_collapse", ctypes.c_int32)]
+                ("collapse_skip", ctypes.c_int32)]
 
 
 class CountInfo(ctypes.Structure):
@@ -76,7 +76,8 @@ class CountInfo(ctypes.Structure):
                 ("enum_words", ctypes.c_int64), ("launches", ctypes.c_int32), ("pieces", ctypes.c_int32),
                 ("words_enum", ctypes.c_int64), ("enum_span_ms", ctypes.c_float),
                 ("enum_longest_unit_ms", ctypes.c_float), ("enum_exit_spread_ms", ctypes.c_float),
-                ("reserved_t", ctypes.c_int32), ("words_exec", ctypes.c_int64), ("collapsed", ctypes.c_int64)]
+                ("reserved_t", ctypes.c_int32), ("words_exec", ctypes.c_int64), ("collapsed", ctypes.c_int64),
+                ("enum_phase_cycles", ctypes.c_int64 * 10)]
 
     def as_dict(self) -> dict:
         return {
@@ -103,6 +104,7 @@ class CountInfo(ctypes.Structure):
             "enum_exit_spread_ms": float(self.enum_exit_spread_ms),
             "words_exec": int(self.words_exec),
             "collapsed": int(self.collapsed),
+            "enum_phase_cycles": [int(x) for x in self.enum_phase_cycles],
         }
 
 
@@ -248,7 +250,7 @@ class Graph:
     def count_ex(self, p: int, q: int, anchor: str = "auto", stats: bool = False,
                  enum_warps: int = 0, time_limit_ms: int = 0,
                  roots: tuple[int, int] | None = None, kernel: str = "bitmap",
-                 position_order: str = "shared", collapse: bool = True) -> tuple[int, dict]:
+                 position_order: str = "shared", collapse: bool | int = True) -> tuple[int, dict]:
         """roots: count only the search trees rooted in this half-open range of
         anchor vertices (give the anchor explicitly when splitting a count).
         kernel: "bitmap" (the default) or "csr" (the sorted-list ablation).
@@ -256,13 +258,15 @@ class Graph:
         "id" (the other side's id order).
         stats: False, True (the full traversal's counters) or "exec" (the
         executed traversal's words and collapsed subtrees).
-        collapse: count small-C_R subtrees in closed form (the default)."""
+        collapse: count small-C_R subtrees in closed form: True (the default
+        slack), False (enter every node) or the slack s = 1..4 (nodes with
+        |C_R| <= q' + s collapse)."""
         opt = CountOptions()
         opt.kernel = {"bitmap": 0, "csr": 1}[kernel]
         opt.position_order = {"shared": 0, "id": 1}[position_order]
         opt.anchor = ANCHORS[anchor]
         opt.collect_stats = 2 if stats == "exec" else (1 if stats else 0)
-        opt.no_collapse = 0 if collapse else 1
+        opt.collapse_skip = 0 if collapse is True else (-1 if collapse is False else int(collapse))
         opt.enum_warps = enum_warps
         opt.time_limit_ms = time_limit_ms
         if roots is not None:

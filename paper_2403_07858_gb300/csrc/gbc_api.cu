@@ -201,6 +201,7 @@ gbc_status gbc_ctx_create(int device, size_t mem_budget_bytes, gbc_ctx_t *out) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)(0.8 * (double)free_b);
+    CK(init_enumerate_tables());
     CK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
     CK(c->lane.create(c->own));
     cudaMemPool_t pool;
@@ -695,7 +696,8 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
     const int n = (int)jobs.size();
     // statistics of the full traversal (1) or of the executed one (2); subtree collapse unless turned off
     const int enum_mode = want_stats ? (opt && opt->collect_stats == 2 ? 2 : 1) : 0;
-    const bool collapse = !(opt && opt->no_collapse);
+    const int collapse = !opt || opt->collapse_skip == 0 ? kCollapseSkipDefault
+                                                          : (opt->collapse_skip < 0 ? -1 : opt->collapse_skip);
     Scratch sc(st);
     Small *d_small = nullptr;
     CK(sc.get(&d_small, n));
@@ -1314,6 +1316,7 @@ static gbc_status count_impl(gbc_graph_t g, int p, int q, const gbc_count_option
         inf.words_enum = (int64_t)hs.words_enum;
         inf.words_exec = (int64_t)hs.words_exec;
         inf.collapsed = (int64_t)hs.collapsed;
+        for (int i = 0; i < 10; ++i) inf.enum_phase_cycles[i] = (int64_t)hs.phase_cycles[i];
         inf.scratch_bytes = (int64_t)J.scratch_bytes;
         if (!J.trivial && J.a.k >= 2) {
             inf.ms_candidates = tm.between(0, 1);

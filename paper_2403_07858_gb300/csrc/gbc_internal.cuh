@@ -153,6 +153,7 @@ struct SearchStats {
     unsigned long long words_exec;  // words of the traversal k_enumerate executes (collapsed subtrees
                                     // as their C_L and T words)
     unsigned long long collapsed;   // subtrees k_enumerate counted in closed form
+    unsigned long long phase_cycles[10];  // SM cycles of k_enumerate's warps per phase (executed traversal)
 };
 
 // Sets the text gbc_last_error() returns on the calling thread.
@@ -341,10 +342,14 @@ cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, cons
 // (d_jobs: a device array of their CountArgs, indexed by the units' job id).
 // d_queue: a zeroed int32 work counter.
 // mode: 0 the count, 1 with the full traversal's statistics, 2 with the words of
-// the executed traversal.  collapse: count subtrees of nodes with |C_R| <= kq + 2
-// in closed form (never in mode 1).
+// the executed traversal.  collapse >= 0: count the subtrees of nodes with
+// |C_R| <= kq + collapse in closed form (never in mode 1); -1: enter every node.
 cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
-                             int mode, bool collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             int mode, int collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
                              cudaStream_t st);
+// The enumeration's constant tables on the current device (once per context).
+cudaError_t init_enumerate_tables();
+// Default of gbc_count_options.collapse_skip.
+constexpr int kCollapseSkipDefault = 4;
 
 }  // namespace gbc

@@ -745,16 +745,18 @@ constexpr int kLeafList = 128;  // nonzero leaf words staged per warp before the
 constexpr int kParents = 64;    // leaf parents per warp (their C_R) whose words may be staged
 constexpr int kTagShift = 24;   // a staged word's tag: parent slot << 24 | word index (< 2^24)
 
+constexpr int kPhases = 10;  // phases whose SM cycles the executed-traversal statistics add up
+
 struct EnumLayout {
     int wr, wl;     // row capacities in words (both even)
     int levels;     // k - 3 (levels with a node whose children are not all leaf parents)
-    int collapse;   // 1: count the subtree of a node with |C_R| <= kq + 2 in closed form
+    int collapse;   // >= 0: count the subtree of a node with |C_R| <= kq + collapse in closed form; -1: off
     // per warp: parents (kParents x uint4) | their word indices (kParents) | leaf masks | leaf tags |
     // levels x (CR | CL | xs) | scalars
     __host__ __device__ int staging_words() const { return kParents * 5 + 2 * kLeafList; }
     __host__ __device__ int level_words() const { return wr + wl + 32; }
     __host__ __device__ int warp_words() const {
-        return (staging_words() + levels * level_words() + 3 * kMaxPQ + 2 + 3) & ~3;
+        return (staging_words() + levels * level_words() + 3 * kMaxPQ + 2 + 2 * kPhases + 3) & ~3;
     }
 };
 
@@ -810,11 +812,48 @@ __device__ __forceinline__ int gather_children(const uint32_t *CL, int WL, int c
 
 constexpr int kSmemBinom = 256;  // C(n, kq) for n < 256 in shared memory (never above 2^128)
 
-// Which subtrees collapse: C_R minus a skip set of s = m - kq positions is one
-// kq-subset per lane, so C(m, s) <= 32; s <= 2 keeps the per-word work small.
-__device__ __forceinline__ bool collapsible(int m, int kq) {
+// Skip sets of the subtree collapse: every s-subset of {0, ..., 15} for s = 2..4
+// as a bit mask, in increasing order of the mask (colexicographic order), so
+// the first C(m, s) entries of row s are exactly the s-subsets of {0..m-1}.
+constexpr int kColexMaxM = 16;
+constexpr int kColexMaxS = 4;
+constexpr int kColexEntries = 120 + 560 + 1820;
+__device__ uint16_t g_colex[kColexEntries];
+__device__ __forceinline__ int colex_row(int s) { return s == 2 ? 0 : (s == 3 ? 120 : 680); }
+constexpr int kCollapseRounds = 8;  // at most 8 x 32 kq-subsets per collapsed node
+
+__host__ __device__ __forceinline__ int binom_small(int m, int s) {
+    return s == 0 ? 1 : s == 1 ? m : s == 2 ? m * (m - 1) / 2
+         : s == 3 ? m * (m - 1) * (m - 2) / 6 : m * (m - 1) * (m - 2) * (m - 3) / 24;
+}
+
+// Which subtrees collapse: those whose C_R exceeds kq by at most max_skip
+// positions; lane t of a round takes C_R minus the t-th skip set of s = m - kq
+// positions, at most kCollapseRounds rounds of 32.
+__device__ __forceinline__ bool collapsible(int m, int kq, int max_skip) {
     const int s = m - kq;
-    return s == 0 || (s == 1 && m <= 32) || (s == 2 && m * (m - 1) <= 64);
+    if (s > max_skip) return false;
+    if (s <= 1) return m <= 32;
+    return s <= kColexMaxS && m <= kColexMaxM && binom_small(m, s) <= 32 * kCollapseRounds;
+}
+
+cudaError_t init_enumerate_tables() {
+    static uint16_t h[kColexEntries];
+    static bool made = false;
+    if (!made) {
+        int at = 0;
+        for (int s = 2; s <= kColexMaxS; ++s) {
+            // Gosper's successor: the next larger mask with the same popcount
+            for (uint32_t v = (1u << s) - 1; v < (1u << kColexMaxM);) {
+                if (at == kColexEntries) return cudaErrorInvalidValue;  // cannot happen: C(16, 2..4) entries
+                h[at++] = (uint16_t)v;
+                const uint32_t lo = v & (0u - v), r = v + lo;
+                v = (((r ^ v) >> 2) / lo) | r;
+            }
+        }
+        made = true;
+    }
+    return cudaMemcpyToSymbol(g_colex, h, sizeof h);
 }
 
 // MODE 0: the count.  MODE 1: the count with the search-tree statistics of the
@@ -867,6 +906,16 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     if (lane == 0) atomicCAS(a0.tail, 0ull, global_ns());
     // each unit's start time, kept in the warp's shared scalars (no register)
     unsigned long long *t_unit = reinterpret_cast<unsigned long long *>(spanp + kMaxPQ);
+    // SM cycles this warp spends per phase (WORK): 0 unit set-up, 1 collapse,
+    // 2 child gather, 3 internal-child tests, 4 descent, 5 leaf-parent nodes
+    // (gross), 6 leaf counting, 7 leaf counting inside 5, 8 lane-serial leaf walks
+    unsigned long long *ph = t_unit + 1;
+    if (WORK && lane == 0)
+        for (int i = 0; i < kPhases; ++i) ph[i] = 0;
+    auto ph_now = [&]() -> long long { return WORK ? clock64() : 0ll; };
+    auto ph_add = [&](int i, long long t0) {
+        if (WORK && lane == 0) ph[i] += (unsigned long long)(clock64() - t0);
+    };
     while (true) {
         int guidx = 0;
         if (lane == 0) guidx = atomicAdd(queue, 1);
@@ -908,6 +957,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         auto r_word = [&](int32_t x, uint32_t wi) { return Rw[2 * ((int64_t)(wi >> 1) * c + x) + (wi & 1u)]; };
         u128 unit_acc = 0;
         if (lane == 0) *t_unit = global_ns();
+        const long long t_setup = ph_now();
         // Collapse of a node's subtree (C_R = cr over nsp pairs holding m
         // positions, C_L = cl from word lo, jrem vertices still to add).  The
         // subtree adds C(|C_R & R_Z|, kq) for every jrem-subset Z of C_L (its
@@ -917,49 +967,50 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         // the same (L, R) pairs counted from the other side (Def. 1).  Lane t
         // takes the t-th Q, i.e. C_R without its skip set of m - kq positions.
         auto collapse = [&](const uint2 *cr, int nsp, int m, const uint32_t *cl, int lo, int jrem, int32_t *posbuf) {
+            const long long tc = ph_now();
             int cur = 0;
             gather_children(reinterpret_cast<const uint32_t *>(cr), 2 * nsp, 64 * nsp, cur, posbuf);
             const int s = m - kq;
             const int pos = lane < m ? posbuf[lane] : 0;
-            const int nsub = s == 0 ? 1 : (s == 1 ? m : m * (m - 1) / 2);
-            uint32_t skip = 0;
-            if (s == 1 && lane < nsub) {
-                skip = 1u << lane;
-            } else if (s == 2 && lane < nsub) {
-                int t = lane, i0 = 0;  // the lane-th pair i0 < i1 < m
-                while (i0 < m - 2 && t >= m - 1 - i0) { t -= m - 1 - i0; ++i0; }
-                skip = (1u << i0) | (1u << (i0 + 1 + t));
-            }
-            int n = 0, nzw = 0;
-            for (int w0 = lo; w0 < WL; w0 += 32) {
-                const uint32_t cwl = w0 + lane < WL ? cl[w0 + lane] : 0u;
-                uint32_t nz = __ballot_sync(kFull, cwl != 0u);
-                if (WORK) nzw += __popc(nz);
-                while (nz) {
-                    const int b = __ffs(nz) - 1;
-                    nz &= nz - 1;
-                    const uint32_t cw = __shfl_sync(kFull, cwl, b);
-                    const uint32_t tv = lane < m ? Tb[(int64_t)(w0 + b) * P + pos] : ~0u;
-                    if (s == 0) {
-                        n += __popc(cw & __reduce_and_sync(kFull, tv));
-                    } else {
-                        uint32_t acc = cw;
-                        for (int l = 0; l < m; ++l) {
-                            const uint32_t v = __shfl_sync(kFull, tv, l);
-                            if (!((skip >> l) & 1u)) acc &= v;
+            const int nsub = binom_small(m, s);
+            int nzw = 0;
+            for (int r0 = 0; r0 < nsub; r0 += 32) {
+                const int t = r0 + lane;  // this lane's Q: C_R without skip set t
+                uint32_t skip = 0;
+                if (s == 1) skip = 1u << t;
+                else if (s >= 2 && t < nsub) skip = g_colex[colex_row(s) + t];
+                int n = 0;
+                for (int w0 = lo; w0 < WL; w0 += 32) {
+                    const uint32_t cwl = w0 + lane < WL ? cl[w0 + lane] : 0u;
+                    uint32_t nz = __ballot_sync(kFull, cwl != 0u);
+                    if (WORK && r0 == 0) nzw += __popc(nz);
+                    while (nz) {
+                        const int b = __ffs(nz) - 1;
+                        nz &= nz - 1;
+                        const uint32_t cw = __shfl_sync(kFull, cwl, b);
+                        const uint32_t tv = lane < m ? Tb[(int64_t)(w0 + b) * P + pos] : ~0u;
+                        if (s == 0) {
+                            n += __popc(cw & __reduce_and_sync(kFull, tv));
+                        } else {
+                            uint32_t acc = cw;
+                            for (int l = 0; l < m; ++l) {
+                                const uint32_t v = __shfl_sync(kFull, tv, l);
+                                if (!((skip >> l) & 1u)) acc &= v;
+                            }
+                            n += __popc(acc);
                         }
-                        n += __popc(acc);
                     }
                 }
-            }
-            if (lane < nsub && n >= jrem) {
-                if (jrem == kq && smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
-                else add_u128(unit_acc, binom_lookup(a.binom, jrem, n, ovf), ovf);
+                if (t < nsub && n >= jrem) {
+                    if (jrem == kq && smem_binom && n < kSmemBinom) add_u128(unit_acc, s_binom[n], ovf);
+                    else add_u128(unit_acc, binom_lookup(a.binom, jrem, n, ovf), ovf);
+                }
             }
             if (WORK && lane == 0) { wk_words += (unsigned long long)(WL - lo) + (unsigned long long)m * nzw; wk_nodes += 1; }
             __syncwarp();
+            ph_add(1, tc);
         };
-        const bool may_collapse = !STATS && lay.collapse && k >= 4;
+        const bool may_collapse = !STATS && lay.collapse >= 0 && k >= 4;
         // level 2 node {u, j}: C_R = R_j, C_L = S_j (bits after j only)
         bool unit_collapsed = false;
         {
@@ -975,7 +1026,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if (lane == 0) { cursor[0] = j + 1; dmask[0] = 0; spanp[0] = sp; }
             mc = __reduce_add_sync(kFull, mc);
             __syncwarp();
-            if (may_collapse && collapsible(mc, kq)) {
+            ph_add(0, t_setup);
+            if (may_collapse && collapsible(mc, kq, lay.collapse)) {
                 collapse(CR(0), sp, mc, CL(0), lo, k - 2, XS(0));
                 unit_collapsed = true;
             }
@@ -989,7 +1041,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
         // the word's leaves add sum_v C(v, kq) * |{x : count = v}|.  A parent's
         // C_R(y) is kept as its (at most four) nonzero words with their word
         // indices in N(u)'s position order, so it may lie anywhere in the row.
-        auto count_leaves = [&](int n_staged) {
+        auto count_leaves = [&](int n_staged, bool inside) {
+            const long long tl = ph_now();
             for (int e0 = 0; e0 < n_staged; e0 += 32) {
                 const int e = e0 + lane;
                 if (e < n_staged) {
@@ -1065,6 +1118,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     }
                 }
             }
+            ph_add(inside ? 7 : 6, tl);
         };
         int lv = 0;
         unsigned batches = 0;
@@ -1072,6 +1126,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             if ((++batches & 1023u) == 0 && __shfl_sync(kFull, (int)past_deadline(a), 0)) break;
             const uint32_t dm = dmask[lv];
             if (dm != 0) {
+                const long long td = ph_now();
                 const int t = __ffs(dm) - 1;
                 const int32_t x = XS(lv)[t];
                 const int sp = spanp[lv];
@@ -1097,7 +1152,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 for (int w = lo + lane; w < WL; w += 32) cl2[w] = cl[w] & St[(int64_t)w * c + x];
                 if (may_collapse) mc = __reduce_add_sync(kFull, mc);
                 __syncwarp();
-                if (may_collapse && collapsible(mc, kq)) {
+                ph_add(4, td);
+                if (may_collapse && collapsible(mc, kq, lay.collapse)) {
                     // the child (|L| = lv + 3) is counted whole, not entered
                     collapse(cr2, nsp, mc, cl2, lo, k - (lv + 3), XS(lv + 1));
                     continue;
@@ -1108,8 +1164,10 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 continue;
             }
             int cur = cursor[lv];
+            const long long tg = ph_now();
             const int got = gather_children(CL(lv), WL, (int)c, cur, XS(lv));
             if (lane == 0) cursor[lv] = cur;
+            ph_add(2, tg);
             if (got == 0) {
                 __syncwarp();
                 if (lv == 0) break;
@@ -1121,6 +1179,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             const uint2 *cr = CR(lv);
             const uint32_t *cl = CL(lv);
             if (ell + 2 == k) {
+                const long long tp = ph_now();
                 // Children y are leaf parents.  Phase A: each lane forms C_R(y) =
                 // C_R & R_y; a child that passes puts it in the warp's parent list
                 // and stages the nonzero words of its leaf set C_L & S_y (after y)
@@ -1206,7 +1265,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                             const bool last = w + 1 == WL;
                             if (nl > kLeafList - 32 || (last && npar > kParents - 32)) {
                                 __syncwarp();
-                                count_leaves(nl);
+                                count_leaves(nl, true);
                                 nl = 0;
                                 if (last) npar = 0;  // every parent's words are staged and counted
                                 __syncwarp();
@@ -1214,6 +1273,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                         }
                     }
                 }
+                const long long tw = ph_now();
                 if (py && !narrow) {
                     // C_R(y) spread over more than four words (rare): the lane walks its
                     // own leaves, C_R(y) & R_x re-read per leaf
@@ -1237,6 +1297,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                     }
                 }
                 __syncwarp();
+                ph_add(8, tw);
+                ph_add(5, tp);
                 if (cur >= c) {  // every child taken: back to the parent at once
                     if (lv == 0) break;
                     --lv;
@@ -1244,6 +1306,7 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 continue;  // no child to enter: the next batch of this node
             }
             // internal children: evaluate both pruning tests, flag those to enter
+            const long long ti = ph_now();
             int n = 0;
             int32_t x = 0;
             if (lane < got) {
@@ -1278,8 +1341,9 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
             __syncwarp();
             if (lane == 0) dmask[lv] = dmb;
             __syncwarp();
+            ph_add(3, ti);
         }
-        if (nl > 0) count_leaves(nl);  // the unit's last staged words
+        if (nl > 0) count_leaves(nl, false);  // the unit's last staged words
         __syncwarp();
         // the unit's sum goes to its job (and to its root when split by root)
         const u128 s = warp_sum_u128(unit_acc, ovf);
@@ -1306,6 +1370,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     if (WORK) {
         atomicAdd(&a0.stats->words_exec, wk_words);
         atomicAdd(&a0.stats->collapsed, wk_nodes);
+        if (lane == 0)
+            for (int i = 0; i < kPhases; ++i) atomicAdd(&a0.stats->phase_cycles[i], ph[i]);
     }
     if (STATS) {
         const CountArgs &a = a0;  // statistics are kept for single-job launches
@@ -1349,9 +1415,9 @@ cudaError_t launch_sort_units(const int2 *units_all, const uint8_t *bucket, cons
 }
 
 cudaError_t launch_enumerate(const CountArgs *d_jobs, const int2 *units, const int32_t *n_units, int32_t *d_queue,
-                             int mode, bool collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
+                             int mode, int collapse, int n_warps_hint, int max_wr, int max_wl, int max_k, int n_sms,
                              cudaStream_t st) {
-    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3), collapse ? 1 : 0};
+    EnumLayout lay{(max_wr + 1) & ~1, (max_wl + 1) & ~1, std::max(1, max_k - 3), collapse};
     if (max_wl >= (1 << kTagShift)) return cudaErrorInvalidValue;  // staged-word tags hold the word index in 24 bits
     const size_t per_warp = (size_t)lay.warp_words() * 4;
     const int warps_per_cta = 8;

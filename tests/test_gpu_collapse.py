@@ -17,24 +17,33 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
+def _collapses(m, kq, slack):
+    """The library's rule: |C_R| = m exceeds kq by s <= slack, and the skip
+    sets fit (s <= 1 with m <= 32; else s <= 4, m <= 16, C(m, s) <= 256)."""
+    s = m - kq
+    if s > slack:
+        return False
+    return m <= 32 if s <= 1 else (s <= 4 and m <= 16 and math.comb(m, s) <= 256)
+
+
 @pytest.mark.parametrize("m,n,p,q", [(30, 6, 6, 6), (30, 7, 6, 6), (30, 8, 6, 6), (24, 4, 5, 2),
-                                     (26, 5, 8, 3), (20, 17, 16, 16), (40, 10, 8, 8), (60, 9, 4, 7)])
+                                     (26, 5, 8, 3), (20, 17, 16, 16), (40, 10, 8, 8), (30, 9, 6, 6),
+                                     (30, 10, 5, 6), (20, 18, 16, 16), (30, 12, 4, 8)])
 def test_complete_graphs_collapse_at_the_units(gpu_ctx, m, n, p, q):
-    """Anchored on U, every level-2 unit of K_{m,n} has |C_R| = n, so n - q =
-    0, 1, 2 collapse at the unit (one, n or C(n, 2) subsets Q; K_{40,10} at
-    (8,8) needs 45 > 32 subsets and (60, 9, 4, 7) a skip set of 2 with 36, so
-    neither collapses); the count is C(m,p) C(n,q)."""
+    """Anchored on U, every level-2 unit of K_{m,n} has |C_R| = n, so with a
+    slack s >= n - q the unit collapses: C(n, n - q) subsets Q, each with every
+    higher candidate; the count is C(m,p) C(n,q) with and without it, at every
+    slack (K_{20,18} at (16,16) needs a skip set of 2 from 18 positions, beyond
+    the 16 the skip-set table covers, so it is always entered)."""
     want = math.comb(m, p) * math.comb(n, q)
     h = gpu_ctx.load(bipgen.complete(m, n))
-    on, info = h.count_ex(p, q, anchor="U", stats="exec")
-    assert on == want
     assert h.count_ex(p, q, anchor="U")[0] == want
     assert h.count_ex(p, q, anchor="U", collapse=False)[0] == want
-    s = n - q
-    if p >= 4 and (s == 0 or (s == 1 and n <= 32) or (s == 2 and n * (n - 1) <= 64)):
-        assert info["collapsed"] > 0
-    elif p >= 4:
-        assert info["collapsed"] == 0
+    for slack in (1, 2, 3, 4):
+        got, info = h.count_ex(p, q, anchor="U", stats="exec", collapse=slack)
+        assert got == want, slack
+        if p >= 4:
+            assert (info["collapsed"] > 0) == _collapses(n, q, slack), slack
     h.close()
 
 
@@ -49,6 +58,8 @@ def test_power_law_graph_collapse_on_and_off(gpu_ctx, p, q):
         got, info = h.count_ex(p, q, anchor=anchor, stats="exec")
         assert got == want, (p, q, anchor)
         assert h.count_ex(p, q, anchor=anchor, collapse=False)[0] == want, (p, q, anchor)
+        for slack in (1, 3, 4):
+            assert h.count_ex(p, q, anchor=anchor, collapse=slack)[0] == want, (p, q, anchor, slack)
         tot, per = h.count_per_root(p, q, anchor)
         assert tot == want and per == per_want, (p, q, anchor)
         k = p if anchor == "U" else q
