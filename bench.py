@@ -358,23 +358,27 @@ def main():
 
     # ---- roofline of the dominant kernel (the enumeration).  ncu shows it bound
     # by instruction issue on the integer pipe with its bitmap rows resident in
-    # L1/L2, so the roofline is ALU.  Algorithmic work per launch: the words of
-    # the traversal the kernel executes -- per evaluated search node ceil(d/32)
-    # C_R words, plus ceil(c/32) C_L words for internal nodes; per collapsed
-    # subtree its C_L words and |C_R| T words per nonzero C_L word -- each word
-    # one AND and one POPC.  Peak: the POPC pipe, the narrower of the two,
-    # retires 16 results per SM per clock (the register-only AND + POPC loop of
-    # gbc_measure_int_peaks reaches that rate), so the SMs can do at most
-    # SMs x 16 x clock words per second, two ops each.
+    # L1/L2, so the roofline is ALU.  Algorithmic work per launch, as the
+    # measurement plan defines it independently of the kernel's design: the
+    # model words of the search nodes of the full traversal below the roots'
+    # children (the oracle's instrumented tree; the statistics pass equals it)
+    # -- per evaluated node ceil(d/32) C_R words, plus ceil(c/32) C_L words for
+    # internal nodes -- each word one AND and one POPC.  The kernel itself
+    # executes fewer: subtrees with a small C_R are counted in closed form, and
+    # the words it does execute (evaluated nodes plus each collapsed subtree's
+    # C_L and T words) are reported beside, with their own fraction.  Peak: the
+    # POPC pipe, the narrower of the two, retires 16 results per SM per clock
+    # (the register-only AND + POPC loop of gbc_measure_int_peaks reaches that
+    # rate), so the SMs can do at most SMs x 16 x clock words per second.
     peaks = _peaks()
     roof = None
-    if enum_launches and exec_words:
+    if enum_launches and model_words:
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         n_sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak_words = n_sms * 16 * sm_max * 1e6
         peak_tops = 2.0 * peak_words / 1e12
-        words_per_launch = sum(exec_words.values()) / len(exec_words)
-        model_per_launch = sum(model_words.values()) / len(model_words)
+        words_per_launch = sum(model_words.values()) / len(model_words)
+        exec_per_launch = sum(exec_words.values()) / len(exec_words) if exec_words else None
         ops_per_launch = 2.0 * words_per_launch
         ms_per_launch = enum_ms / enum_launches
         achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e12
@@ -384,18 +388,18 @@ def main():
                 "peak_source": f"derived: {n_sms} SMs x 16 POPC/clk/SM x {sm_max:.0f} MHz max SM clock "
                                "= words/s, x 2 ops (AND + POPC) per word",
                 "algorithmic_ops_per_launch": ops_per_launch, "ops_per_word": 2,
-                "executed_words_per_launch": words_per_launch,
-                "collapsed_subtrees_per_launch": collapsed / len(exec_words),
-                "full_traversal_model_words_per_launch": model_per_launch,
-                "full_traversal_model_words_per_s_over_peak": model_per_launch / (ms_per_launch * 1e-3) / peak_words,
+                "model_words_per_launch": words_per_launch,
+                "executed_words_per_launch": exec_per_launch,
+                "executed_frac": (exec_per_launch / (ms_per_launch * 1e-3) / peak_words) if exec_per_launch else None,
+                "collapsed_subtrees_per_launch": collapsed / len(exec_words) if exec_words else None,
                 "loaded_words_per_launch_full_traversal": enum_words / len(model_words),
                 "launches": enum_launches, "ms_per_launch": ms_per_launch, "tail": tail,
                 "int32_lanes_peak_tops": n_sms * 128 * sm_max * 1e6 / 1e12,
                 "microbench": {
                     "and_popc_add_loop_words_per_s": micro["and_popc_words_per_s"],
                     "loop_over_derived_peak": micro["and_popc_words_per_s"] / peak_words,
-                    "executed_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
-                                                      / micro["and_popc_words_per_s"],
+                    "model_words_per_s_over_loop": words_per_launch / (ms_per_launch * 1e-3)
+                                                   / micro["and_popc_words_per_s"],
                     "l2_and_popc_stream_gbs": micro["l2_bytes_per_s"] / 1e9}}
 
     # ---- the dense-core and the 256-graph batch workloads (extra keys of the line)

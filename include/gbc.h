@@ -202,7 +202,8 @@ typedef struct {
                                       2 child gathers, 3 internal-child tests, 4 descents, 5 nodes
                                       whose children are leaf parents (gross: includes 7 and 8),
                                       6 leaf counting at unit ends, 7 leaf counting inside 5,
-                                      8 lane-serial leaf walks inside 5, 9 unused */
+                                      8 lane-serial leaf walks inside 5, 9 children with
+                                      |C_R| = q' counted whole by one lane (inside 3, lane 0's) */
 } gbc_count_info;
 
 /* gbc_count with options and facts (either pointer may be NULL). */

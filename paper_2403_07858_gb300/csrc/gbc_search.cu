@@ -908,7 +908,8 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
     unsigned long long *t_unit = reinterpret_cast<unsigned long long *>(spanp + kMaxPQ);
     // SM cycles this warp spends per phase (WORK): 0 unit set-up, 1 collapse,
     // 2 child gather, 3 internal-child tests, 4 descent, 5 leaf-parent nodes
-    // (gross), 6 leaf counting, 7 leaf counting inside 5, 8 lane-serial leaf walks
+    // (gross), 6 leaf counting, 7 leaf counting inside 5, 8 lane-serial leaf walks,
+    // 9 children with |C_R| = kq counted by their own lane (inside 3; lane 0's)
     unsigned long long *ph = t_unit + 1;
     if (WORK && lane == 0)
         for (int i = 0; i < kPhases; ++i) ph[i] = 0;
@@ -1321,7 +1322,28 @@ k_enumerate(const CountArgs *jobs, const int2 *units, const int32_t *n_units, in
                 int m = 0;
                 for (int w = lo; w < WL; ++w) m += __popc(cl[w] & St[(int64_t)w * c + x]);
                 if (STATS) words += WL - lo;
-                desc = m >= k - (ell + 1);
+                const int jrem = k - (ell + 1);  // vertices the child still has to add
+                desc = m >= jrem;
+                if (desc && may_collapse && n == kq) {
+                    // |C_R(x)| = kq: the child's subtree is C(n_Q, jrem) for the one
+                    // Q = C_R(x), n_Q = |C_L(x) & T_Q|; this lane counts it alone
+                    const long long tq = ph_now();
+                    int nq = 0, loads = 0;
+                    for (int w = lo; w < WL; ++w) {
+                        uint32_t acc = cl[w] & St[(int64_t)w * c + x];
+                        const uint32_t *Tw = Tb + (int64_t)w * P;
+                        for (int pw = 0; pw < sp && acc; ++pw) {
+                            const uint2 v = and2(cr[pw], Rp[pw * c + x]);
+                            for (uint32_t b = v.x; b && acc; b &= b - 1) acc &= Tw[pw * 64 + __ffs(b) - 1], ++loads;
+                            for (uint32_t b = v.y; b && acc; b &= b - 1) acc &= Tw[pw * 64 + 32 + __ffs(b) - 1], ++loads;
+                        }
+                        nq += __popc(acc);
+                    }
+                    if (nq >= jrem) add_u128(unit_acc, binom_lookup(a.binom, jrem, nq, ovf), ovf);
+                    if (WORK) { wk_words += (unsigned long long)(WL - lo) + loads; wk_nodes += 1; }
+                    desc = false;
+                    ph_add(9, tq);
+                }
             }
             const unsigned dmb = __ballot_sync(kFull, desc);
             if (WORK) {
