@@ -24,6 +24,8 @@ wall time adds up the segments).
     python tests/golden/oracle_full_counts.py --workload powerlaw2m [--cores N]
     python tests/golden/oracle_full_counts.py --workload dense_core
     python tests/golden/oracle_full_counts.py --workload powerlaw2m --only 6:6 --checkpoint ck.jsonl
+    python tests/golden/oracle_full_counts.py --workload powerlaw2m --only 6:6 --checkpoint ck.jsonl \
+        --store-partial --budget-s 21600
 """
 from __future__ import annotations
 
@@ -204,6 +206,27 @@ def run_count(g, make, p, q, anchor, cores, budget_s, log, checkpoint=None):
     }
 
 
+def partial_record(g, p, q, anchor, checkpoint, budget_s):
+    """The record of a count the oracle did not finish: every root of the
+    checkpoint (roots taken in descending degree, the heaviest first) with its
+    exact value and time, and the wall time spent."""
+    chunks, wall = _read_checkpoint(checkpoint, f"{p},{q},{anchor}")
+    done = {}
+    for rec in chunks:
+        for r, x, t in zip(rec["roots"], rec["vals"], rec["secs"]):
+            done[int(r)] = (str(int(x)), round(float(t), 3))
+    n_a = g.n_u if anchor == "U" else g.n_v
+    cores = max(1, round(sum(t for _, t in done.values()) / max(wall, 1e-9)))
+    return {"p": p, "q": q, "anchor": anchor,
+            "unavailable": f"oracle unavailable at this size (budget {budget_s:.0f} s wall on about {cores} cores): "
+                           f"{len(done)} of {n_a} roots finished",
+            "roots_done": len(done), "roots_total": n_a,
+            "order": "roots in descending degree (ties by id), the heaviest first",
+            "per_root_done": {str(r): v for r, (v, _) in sorted(done.items())},
+            "per_root_oracle_s": {str(r): t for r, (_, t) in sorted(done.items())},
+            "oracle_core_s": round(sum(t for _, t in done.values()), 1), "oracle_wall_s": round(wall, 1)}
+
+
 def trim_samples(rec: dict, seed: int = 7) -> None:
     """Cut every stored sample to at most MAX_SAMPLE roots by a seeded uniform
     subsample (a uniform subsample of a probability-proportional-to-time sample
@@ -228,6 +251,9 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated p,q pairs as p:q (default all)")
     ap.add_argument("--checkpoint", default="",
                     help="append every finished chunk to this JSON-lines file and resume from it")
+    ap.add_argument("--store-partial", action="store_true",
+                    help="with --checkpoint and one --only pair: store the roots the checkpoint finished "
+                         "(exact per-root values) as that count's record, marked unavailable at this size")
     args = ap.parse_args()
     if args.trim_samples:
         rec = json.load(open(OUT))
@@ -245,6 +271,16 @@ def main():
     entry["sha256"] = bipgen.graph_sha256(g)
     entry["machine"] = {"cpu": _cpu_model(), "arch": platform.machine()}
     only = {tuple(int(x) for x in s.split(":")) for s in args.only.split(",") if s}
+    if args.store_partial:
+        (p, q), = only
+        anchor = next(a for pp, qq, a in w["counts"] if (pp, qq) == (p, q))
+        entry["counts"][f"{p},{q}"] = partial_record(g, p, q, anchor, args.checkpoint, args.budget_s)
+        rec[args.workload] = entry
+        with open(OUT + ".tmp", "w") as f:
+            json.dump(rec, f, indent=1, sort_keys=True)
+            f.write("\n")
+        os.replace(OUT + ".tmp", OUT)
+        return
 
     def log(msg):
         print(msg, flush=True)

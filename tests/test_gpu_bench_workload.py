@@ -60,6 +60,22 @@ def test_whole_counts_equal_the_oracle(gpu_ctx, powerlaw, stored, k):
     h.close()
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
+def test_heaviest_degree_roots_of_unfinished_counts(gpu_ctx, powerlaw, stored, k):
+    """A count the oracle could not finish within its budget stores the roots
+    it did finish, heaviest degree first, with their exact values: the GPU's
+    per-root values must match every one of them."""
+    res = stored.get(f"{k},{k}")
+    if res is None or "per_root_done" not in res:
+        pytest.skip(f"no partial oracle record for p=q={k}")
+    h = gpu_ctx.load(powerlaw)
+    tot, per = h.count_per_root(k, k, res["anchor"])
+    assert len(res["per_root_done"]) == res["roots_done"] > 0
+    for r, v in res["per_root_done"].items():
+        assert per[int(r)] == int(v), (k, r)
+    h.close()
+
+
 @pytest.mark.parametrize("k,n_sample", [(2, 24), (3, 24), (4, 16), (5, 12), (6, 8)])
 def test_sampled_roots_match_the_oracle(gpu_ctx, powerlaw, k, n_sample):
     g = powerlaw
