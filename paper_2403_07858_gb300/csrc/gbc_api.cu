@@ -1147,21 +1147,38 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             used += need;
             wave.push_back(i);
         }
-        std::vector<CountArgs> enum_jobs;
-        int max_wr = 2, max_wl = 2, max_k = 4;
-        // live units of the wave's enumeration, shared by its counts
-        int64_t unit_cap = 0;
+        // The wave's enumeration runs one persistent launch per |L| on the anchor
+        // side: each launch's shared-memory layout (levels, row widths) is the
+        // largest of its own counts', so a deep count's layout does not lower
+        // the occupancy of the others.  Counts with the same |L| share a launch.
+        struct EnumGroup {
+            int k = 0;
+            std::vector<CountArgs> jobs;
+            int max_wr = 2, max_wl = 2;
+            int64_t unit_cap = 0;
+            int2 *units_all = nullptr, *units_sorted = nullptr;
+            uint8_t *units_bucket = nullptr;
+            int32_t *ucounters = nullptr;  // n_all, bucket_count[16], cursor[16]
+            std::vector<int> ids;
+        };
+        std::vector<EnumGroup> groups;
+        auto group_of = [&](int k) -> EnumGroup & {
+            for (EnumGroup &G : groups)
+                if (G.k == k) return G;
+            groups.emplace_back();
+            groups.back().k = k;
+            return groups.back();
+        };
         for (int i : wave)
-            if (jobs[i].a.k >= 4) unit_cap += jobs[i].a.n_cand;
-        int2 *units_all = nullptr, *units_sorted = nullptr;
-        uint8_t *units_bucket = nullptr;
-        int32_t *ucounters = nullptr;  // n_all, bucket_count[16], cursor[16]
-        if (unit_cap > 0) {
-            CK(wave_sc.get(&units_all, unit_cap));
-            CK(wave_sc.get(&units_sorted, unit_cap));
-            CK(wave_sc.get(&units_bucket, unit_cap));
-            CK(wave_sc.get(&ucounters, 33));
-            CK(cudaMemsetAsync(ucounters, 0, 33 * 4, st));
+            if (jobs[i].a.k >= 4) group_of(jobs[i].a.k).unit_cap += jobs[i].a.n_cand;
+        std::sort(groups.begin(), groups.end(), [](const EnumGroup &x, const EnumGroup &y) { return x.k > y.k; });
+        for (EnumGroup &G : groups) {
+            if (G.unit_cap <= 0) continue;
+            CK(wave_sc.get(&G.units_all, G.unit_cap));
+            CK(wave_sc.get(&G.units_sorted, G.unit_cap));
+            CK(wave_sc.get(&G.units_bucket, G.unit_cap));
+            CK(wave_sc.get(&G.ucounters, 33));
+            CK(cudaMemsetAsync(G.ucounters, 0, 33 * 4, st));
         }
         for (int i : wave) {
             CountArgs &a = jobs[i].a;
@@ -1177,10 +1194,11 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
             if (a.k >= 4) {
                 CK(wave_sc.get(&a.S, h.totals[2]));
                 CK(cudaMemsetAsync(a.S, 0, std::max<int64_t>(h.totals[2], 1) * 4, st));
-                a.units_all = units_all;
-                a.units_bucket = units_bucket;
-                a.n_units_all = ucounters;
-                a.bucket_count = ucounters + 1;
+                EnumGroup &G = group_of(a.k);
+                a.units_all = G.units_all;
+                a.units_bucket = G.units_bucket;
+                a.n_units_all = G.ucounters;
+                a.bucket_count = G.ucounters + 1;
             }
         }
         CK(fork());
@@ -1189,14 +1207,15 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
         for (int i : wave) {
             CountArgs &a = jobs[i].a;
             const Small &h = hs[i];
-            if (a.k >= 4) a.job_id = (int32_t)enum_jobs.size();
+            if (a.k >= 4) a.job_id = (int32_t)group_of(a.k).jobs.size();
             if (csr) continue;
             CK(launch_pairs(a, ctx->n_sms, sj(i)));
             if (a.k >= 4) {
-                enum_jobs.push_back(a);
-                max_wr = std::max(max_wr, (int)row_stride(a.g.maxdegA));
-                max_wl = std::max(max_wl, (std::max(h.cand_max, 1) + 31) / 32);
-                max_k = std::max(max_k, a.k);
+                EnumGroup &G = group_of(a.k);
+                G.jobs.push_back(a);
+                G.ids.push_back(i);
+                G.max_wr = std::max(G.max_wr, (int)row_stride(a.g.maxdegA));
+                G.max_wl = std::max(G.max_wl, (std::max(h.cand_max, 1) + 31) / 32);
             }
         }
         CK(join());
@@ -1218,21 +1237,26 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                 CK(launch_enumerate_csr(a, C, warps, want_stats, st));
             }
             CK(cudaStreamSynchronize(st));
-            enum_jobs.clear();
+            for (EnumGroup &G : groups) G.jobs.clear();
         }
-        if (!enum_jobs.empty()) {
+        bool launched = false;
+        for (EnumGroup &G : groups) {
+            if (G.jobs.empty()) continue;
             CountArgs *d_jobs = nullptr;
             int32_t *d_queue = nullptr;
-            CK(wave_sc.get(&d_jobs, enum_jobs.size()));
+            CK(wave_sc.get(&d_jobs, G.jobs.size()));
             CK(wave_sc.get(&d_queue, 1));
             CK(cudaMemsetAsync(d_queue, 0, 4, st));
-            CK(cudaMemcpyAsync(d_jobs, enum_jobs.data(), sizeof(CountArgs) * enum_jobs.size(),
+            CK(cudaMemcpyAsync(d_jobs, G.jobs.data(), sizeof(CountArgs) * G.jobs.size(),
                                cudaMemcpyHostToDevice, st));
-            CK(launch_sort_units(units_all, units_bucket, ucounters, ucounters + 1, ucounters + 17, units_sorted,
-                                 unit_cap, st));
-            CK(launch_enumerate(d_jobs, units_sorted, ucounters, d_queue, enum_mode, collapse, warps_for(wave),
-                                max_wr, max_wl, max_k, ctx->n_sms, st));
-            // the job table is read by the launch: keep the host copy alive until it has run
+            CK(launch_sort_units(G.units_all, G.units_bucket, G.ucounters, G.ucounters + 1, G.ucounters + 17,
+                                 G.units_sorted, G.unit_cap, st));
+            CK(launch_enumerate(d_jobs, G.units_sorted, G.ucounters, d_queue, enum_mode, collapse, warps_for(G.ids),
+                                G.max_wr, G.max_wl, G.k, ctx->n_sms, st));
+            launched = true;
+        }
+        if (launched) {
+            // the job tables are read by the launches: keep the host copies alive until they have run
             if (on_done) CK(wait_releasing(wave));
             else CK(cudaStreamSynchronize(st));
         } else if (on_done) {
