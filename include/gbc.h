@@ -290,7 +290,8 @@ void gbc_list_end(gbc_lister_t l);
  * gbc_count_batch -- many counts, possibly on different graphs of this context,
  * in one pipeline: every stage runs for all jobs before the host waits, and the
  * enumeration (Alg. 1's search below the roots' children, Sec. IV) of all jobs
- * is one persistent launch over their concatenated level-2 work units.
+ * is one persistent launch per set size |L| over the concatenated level-2 work
+ * units of the jobs with that size (each launch laid out for its own jobs).
  *   graphs[n], p[n], q[n]: host arrays; graphs must belong to ctx;
  *   out[n]: host, the count of job i when per_job[i] == GBC_OK;
  *   per_job[n]: host, each job's status (GBC_ERR_ARG, _OOM, _OVERFLOW, ...).
