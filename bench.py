@@ -722,7 +722,7 @@ def serve_workload(args, rank, world, local):
                 except gbc.CountTimeout:
                     status[i] = "timeout"
                 except gbc.GbcError as e:
-                    status[i] = f"error {e.status}: {str(e)[:120]}"
+                    status[i] = f"error {e.status}: {str(e)[:400]}"
                 done_at[i] = time.perf_counter() - start
 
             for i, (gi, p, q) in enumerate(qs):

@@ -683,6 +683,12 @@ static size_t wave_need(int k, const int64_t totals[3], int64_t nE) {
 // scans, and one at the end, whatever the number of jobs.  The enumeration of
 // all jobs with |L| >= 4 is one persistent launch (a job table on the device).
 // Per-job scratch is granted in waves that fit the context's budget.
+// The enumeration launch sets its kernel's dynamic shared-memory limit to the
+// launch's own size just before launching; counts on several host threads
+// (serving workers) must not interleave those two steps, or one thread's
+// smaller limit undercuts another thread's launch.
+static std::mutex g_enum_launch_mu;
+
 // on_done (optional): called for each job as soon as its outcome is known --
 // jobs that end early (trivial, |L| <= 2, no candidates) at the host
 // synchronisations, the others when their last kernel work is done, which the
@@ -1032,9 +1038,12 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                 CK(cudaMemsetAsync(d_queue, 0, 4, st));
                 CK(cudaMemcpyAsync(d_job, &b, sizeof(CountArgs), cudaMemcpyHostToDevice, st));
                 CK(launch_sort_units(u_all, u_bucket, ucnt, ucnt + 1, ucnt + 17, u_sorted, nc, st));
-                CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, enum_mode, collapse, warps_for(std::vector<int>{i}),
-                                    (int)row_stride(a.g.maxdegA), (std::max(hs[i].cand_max, 1) + 31) / 32, a.k,
-                                    ctx->n_sms, st));
+                {
+                    std::lock_guard<std::mutex> lk(g_enum_launch_mu);
+                    CK(launch_enumerate(d_job, u_sorted, ucnt, d_queue, enum_mode, collapse,
+                                        warps_for(std::vector<int>{i}), (int)row_stride(a.g.maxdegA),
+                                        (std::max(hs[i].cand_max, 1) + 31) / 32, a.k, ctx->n_sms, st));
+                }
             }
             CK(cudaStreamSynchronize(st));  // b is read by the launch
             J.scratch_bytes = std::max(J.scratch_bytes, sc.bytes + psc.bytes);
@@ -1251,8 +1260,11 @@ static gbc_status run_jobs(gbc_ctx_s *ctx, Lane &lane, size_t budget, std::vecto
                                cudaMemcpyHostToDevice, st));
             CK(launch_sort_units(G.units_all, G.units_bucket, G.ucounters, G.ucounters + 1, G.ucounters + 17,
                                  G.units_sorted, G.unit_cap, st));
-            CK(launch_enumerate(d_jobs, G.units_sorted, G.ucounters, d_queue, enum_mode, collapse, warps_for(G.ids),
-                                G.max_wr, G.max_wl, G.k, ctx->n_sms, st));
+            {
+                std::lock_guard<std::mutex> lk(g_enum_launch_mu);
+                CK(launch_enumerate(d_jobs, G.units_sorted, G.ucounters, d_queue, enum_mode, collapse,
+                                    warps_for(G.ids), G.max_wr, G.max_wl, G.k, ctx->n_sms, st));
+            }
             launched = true;
         }
         if (launched) {

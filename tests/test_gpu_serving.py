@@ -205,3 +205,32 @@ def test_admission_keeps_batches_within_the_budget():
             h.close()
     finally:
         ctx.close()
+
+
+def test_concurrent_batches_with_different_layouts():
+    """Four workers put batches of different |L| and row widths on the device at
+    once (each enumeration launch sizes its own shared memory): every request
+    of repeated bursts must finish with the oracle's count."""
+    import paper_2403_07858_gb300 as gbc
+    gbc.build()
+    ctx = gbc.Context(0)
+    try:
+        graphs = _graphs()
+        hs = [ctx.load(g) for g in graphs]
+        want = _oracle_counts(graphs)
+        queries = [(gi, p, q) for gi in range(len(hs)) for p in range(3, 6) for q in range(3, 6)]
+        ctx.serve_start(workers=4, max_batch=4)
+        for burst in range(3):
+            rng = random.Random(1000 + burst)
+            order = queries * 2
+            rng.shuffle(order)
+            tickets = [(qr, ctx.submit(hs[qr[0]], qr[1], qr[2])) for qr in order]
+            for qr, t in tickets:
+                assert ctx.poll(t, -1) == want[qr], (burst, qr)
+        st = ctx.serve_stats()
+        assert st["batches"] >= 3 * len(queries) * 2 // 4
+        ctx.serve_stop()
+        for h in hs:
+            h.close()
+    finally:
+        ctx.close()
