@@ -804,11 +804,15 @@ def ablation_workload(args, local, limit_ms=60_000):
         for p, q in pairs:
             n, info = h.count_ex(p, q)
             row = {"graph": name, "p": p, "q": q, "anchor": info["anchor"], "count": str(n)}
-            for kern in ("bitmap", "csr"):
+            # the bitmap kernel with its subtree collapse off walks the same tree as
+            # the CSR kernel (the representation alone differs); with it on, the
+            # library's default, beside
+            for kern, collapse in (("bitmap", False), ("csr", False), ("bitmap_collapse", True)):
                 ms, ok = [], True
                 for rep in range(1 + max(1, args.steps)):
                     try:
-                        m, inf = h.count_ex(p, q, anchor=info["anchor"], kernel=kern,
+                        m, inf = h.count_ex(p, q, anchor=info["anchor"], kernel=kern.split("_")[0],
+                                            collapse=collapse,
                                             time_limit_ms=limit_ms if kern == "csr" else 0)
                     except gbc.CountTimeout:
                         ok = False
@@ -828,7 +832,9 @@ def ablation_workload(args, local, limit_ms=60_000):
     print(json.dumps({"metric": "time per (p,q) count, bitmap vs sorted-list (CSR) sets", "unit": "ms",
                       "steps": args.steps, "rows": rows,
                       "how": "device time (CUDA events on the library's stream) of gbc_count_ex with "
-                             "kernel = bitmap and kernel = csr, the same anchor and search tree"}), flush=True)
+                             "kernel = bitmap and kernel = csr, the same anchor and search tree (subtree "
+                             "collapse off); bitmap_collapse: the bitmap kernel with its default collapse"}),
+          flush=True)
 
 
 def _relabel(g, new_u, new_v):
